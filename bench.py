@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the Monte-Carlo snakuscule hot path on GB300.
+
+One step = the whole path over one synthetic image: ingest the voxels into the
+library's volume (a1), seed the lattice (a2), evolve every contour for T
+iterations (a3-a8: Philox samples, trilinear gathers from TMA-staged bricks,
+compensated warp reductions, gradient steps) and localize (a9: energy cull and
+overlap competition, cells copied to the host).
+
+Metric: MC contour samples per second (contours x samples x iterations per step /
+step time), the default workload being the 4096x4096 2D image with ~12k nuclei
+(stride-6 lattice, 128 samples, 100 iterations).  `value` is measured with the
+input already in HBM; `e2e` repeats the step through the same C ABI from pinned
+host memory (host-to-device copy of the image and device-to-host copy of the cells
+inside the timed region).  The roofline entry covers the evolution kernel (plain
+ALU issue bound), `cpu_baseline` times the FP64 oracle on the host cores on a
+bounded sample of the same workload.
+
+With torchrun (N > 1) every rank processes its own image (weak scaling, replicas:
+contours never interact across images); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic ALU work per sample, in issue slots (a warp instruction issued for
+# 32 lanes counts 32): Philox4x32-10, uniform conversion, ball/disk map, tap
+# setup, gather and interpolation, weight bands, compensated accumulation.  The
+# derivation is tabulated in the design notes.
+ALG_SLOTS_PER_SAMPLE = {2: 115.0, 3: 177.0}
+SM_COUNT = 152
+LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
+SM_MAX_MHZ = 2070.0
+
+WORKLOADS = {
+    "large-2d": dict(ndim=2, stride=6.0, N=128, T=100, seed=1,
+                     desc="4096x4096 uint8, ~12k disks r 5-10, blur 1.5 + Poisson; stride-6 lattice (465,124 "
+                          "contours), 128 samples, 100 iterations"),
+    "brain-3d": dict(ndim=3, stride=6.0, N=512, T=100, seed=2,
+                     desc="1024x1024x256 uint16 spacing 1:1:2, ~100k ellipsoids, log-normal brightness, ramp + "
+                          "noise; stride-6 lattice (2,456,500 contours), 512 samples, 100 iterations"),
+    "small-3d": dict(ndim=3, stride=4.0, N=256, T=50, seed=0,
+                     desc="64x64x32 uint8, 20 balls r 4-6, noise 15; stride-4 lattice (2048 contours), 256 samples, "
+                          "50 iterations"),
+}
+
+
+def make_input(name: str, seed: int, dtype: str):
+    from paper_1804_06304_gb300 import synth
+    if name == "large-2d":
+        s = synth.large_2d(seed)
+    elif name == "brain-3d":
+        s = synth.brain_3d(seed, with_f16=(dtype == "f16"))
+    else:
+        s = synth.small_3d(seed)
+    vol = s.volume_f16 if dtype == "f16" else s.volume
+    return s, np.ascontiguousarray(vol)
+
+
+def lattice_count(shape_xyz, spacing, stride, ndim):
+    c = 1
+    for d in range(ndim):
+        c *= max(1, int(math.floor(shape_xyz[d] * spacing[d] / stride)))
+    return c
+
+
+# ------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.out = None
+        self.uuid = uuid
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [l.strip().split(",") for l in self.out.read().splitlines() if l.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ oracle leg
+def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0):
+    """Time the FP64 oracle (all host cores) on a random subset of the workload's
+    contours, sized to take about `seconds`; returns (samples/s, threads, sample text)."""
+    from oracle import oracle
+    from paper_1804_06304_gb300 import ac as _ac_defaults  # noqa: F401  (defaults only)
+    ndim = wl["ndim"]
+    seeds = oracle.seed_lattice(ndim, s.shape_xyz, spacing, wl["stride"])
+    R0 = seeds[0, 3]
+    op = oracle.make_params(ndim, wl["N"], wl["T"], eps0=8 * R0 * R0 / s.contrast, dR=1.0,
+                            Rmin=max(0.5, 0.5 * R0), Rmax=3 * R0, max_step=0.5, seed=7)
+    img = oracle.VolumeImage(vol, spacing)
+    threads = oracle.max_threads()
+    rng = np.random.default_rng(rng_seed)
+    pilot = min(len(seeds), max(threads * 2, 16))
+    idx = rng.choice(len(seeds), pilot, replace=False)
+    t0 = time.perf_counter()
+    oracle.evolve(img, op, seeds[idx], ids=idx)
+    dt = time.perf_counter() - t0
+    per = dt / pilot
+    m = int(min(len(seeds), max(pilot, seconds / max(per, 1e-9))))
+    idx = rng.choice(len(seeds), m, replace=False)
+    t0 = time.perf_counter()
+    oracle.evolve(img, op, seeds[idx], ids=idx)
+    dt = time.perf_counter() - t0
+    samples = m * wl["N"] * wl["T"]
+    return samples / dt, threads, f"{m} of {len(seeds)} contours (random, seed {rng_seed}), all {wl['T']} iterations"
+
+
+# ------------------------------------------------------------------------ main
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large-2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="native", choices=["native", "f16"])
+    ap.add_argument("--path", default="brick", choices=["brick", "plain"])
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--compensated", type=int, default=1)
+    ap.add_argument("--brick", type=str, default="0,0,0")
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("need --steps >= 1 and --warmup >= 0")
+
+    if args.impl == "reference":
+        return reference_arm(args, wl, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1804_06304_gb300 import ac
+
+    dist_on = world > 1
+    if dist_on:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    s, vol = make_input(args.workload, wl["seed"] + rank, args.dtype)
+    spacing = s.spacing
+    ndim = wl["ndim"]
+    C_expected = lattice_count(s.shape_xyz, spacing, wl["stride"], ndim)
+    vol_dev = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).to(dev)
+    vol_pin = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).pin_memory()
+    dcode = {np.dtype(np.uint8): ac.AC_U8, np.dtype(np.uint16): ac.AC_U16, np.dtype(np.float16): ac.AC_F16}[vol.dtype]
+
+    V = ac.ac_create_volume(vol_dev, spacing, dtype=dcode)
+    C = ac.ac_seed(V, stride=wl["stride"])
+    assert C.count == C_expected, (C.count, C_expected)
+    R0 = wl["stride"] / math.sqrt(1.5)
+    params = ac.default_params(ndim, R0, s.contrast, N=wl["N"], T=wl["T"], seed=1000 + rank,
+                               path=ac.AC_PATH_BRICK if args.path == "brick" else ac.AC_PATH_PLAIN,
+                               lanes_per_contour=args.lanes, compensated=args.compensated,
+                               brick=tuple(int(x) for x in args.brick.split(",")), warps_per_block=args.warps)
+    E0 = ac.default_E0(ndim, s.contrast)
+
+    def step(src):
+        ac.ac_load_volume(V, src)
+        ac.ac_reseed(C)
+        ac.ac_evolve(C, params)
+        return ac.ac_localize(C, E0)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    for _ in range(args.warmup):
+        step(vol_dev)
+    torch.cuda.synchronize()
+    if dist_on:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    launches0 = ac.ac_kernel_launches()
+    n_cells = 0
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        ev0[i].record()
+        cells = step(vol_dev)
+        ev1[i].record()
+        kernel_ms.append(ac.ac_evolve_kernel_ms(C))
+        n_cells = len(cells)
+    torch.cuda.synchronize()
+    launches = ac.ac_kernel_launches() - launches0
+    if dist_on:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_ms = float(np.mean(step_ms))
+    k_ms = float(np.mean(kernel_ms))
+    if dist_on:
+        t = torch.tensor([t_ms, k_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms, k_ms = float(t[0]), float(t[1])
+
+    samples = C.count * wl["N"] * wl["T"]
+    value = world * samples / (t_ms * 1e-3)
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms = []
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        for i in range(args.steps):
+            flush.zero_()
+            b0.record()
+            cells = step(vol_pin)
+            b1.record()
+            b1.synchronize()
+            e2e_ms.append(b0.elapsed_time(b1))
+        e_ms = float(np.mean(e2e_ms))
+        if dist_on:
+            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t[0])
+        e2e = {"value": world * samples / (e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(len(cells) * 24 + 4 * 6)}
+
+    achieved = ALG_SLOTS_PER_SAMPLE[ndim] * samples / (k_ms * 1e-3) / 1e12
+    peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
+            "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
+            "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, thr, desc = oracle_sample(s, vol, wl, spacing, args.cpu_seconds)
+        cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "MC contour samples/s (whole path: ingest, seed, evolve, localize)",
+            "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 arithmetic on " + str(vol.dtype) + " voxels", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "contours": C.count, "samples": wl["N"],
+                       "iterations": wl["T"], "path": args.path, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "voxels_per_s": world * int(np.prod(vol.shape)) / (t_ms * 1e-3),
+            "evolve_samples_per_s": world * samples / (k_ms * 1e-3),
+            "cells": n_cells,
+            "gpu_launches": int(launches),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        }
+        print(json.dumps(line))
+    if dist_on:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, wl, rank, world):
+    """The FP64 oracle timed on the host cores: each step a bounded random sample of
+    the same workload's contours (all iterations)."""
+    if rank != 0:
+        return
+    s, vol = make_input(args.workload, wl["seed"], args.dtype)
+    per_step = max(2.0, min(15.0, 120.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        oracle_sample(s, vol, wl, s.spacing, per_step, rng_seed=100 + i)
+    vals, thr, desc = [], 0, ""
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        v, thr, desc = oracle_sample(s, vol, wl, s.spacing, per_step, rng_seed=i)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    C = lattice_count(s.shape_xyz, s.spacing, wl["stride"], wl["ndim"])
+    line = {"impl": "reference", "metric": "MC contour samples/s (whole path: ingest, seed, evolve, localize)",
+            "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "contours": C, "samples": wl["N"],
+                       "iterations": wl["T"]},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": thr, "kind": "oracle",
+                             "sample": f"per step: {desc}"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

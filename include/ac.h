@@ -1,0 +1,241 @@
+/*
+ * ac.h -- C ABI of the GB300 Monte-Carlo snakuscule library (libac.so).
+ *
+ * Method: Lotfollahi et al., "Three-Dimensional GPU-Accelerated Active Contours
+ * for Automated Localization of Cells in Large Images" (arXiv:1804.06304).  Many
+ * symmetric contours (spheres in 3D, disks in 2D) are seeded on a lattice over an
+ * image, each evolves independently by gradient descent on its energy (Eqs. 5-15),
+ * estimated by Monte-Carlo sampling of the ball of radius R + dR/2 (section
+ * "Monte-Carlo Integration"), and the converged contours are culled by energy and
+ * merged by overlap competition into cell locations (section "Results and
+ * Discussion").
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an ac_status; nothing throws across the ABI.  On a
+ *     failure ac_last_error() returns a message for the calling thread.
+ *   - The library owns every device allocation it makes, through the opaque
+ *     handles below.  The caller owns host buffers and the CUDA stream
+ *     (`cuda_stream` is a cudaStream_t; NULL means the legacy default stream).
+ *   - Calls are asynchronous on that stream unless documented as synchronizing.
+ *   - Positions are physical: voxel (i, j, k) has its centre at
+ *     (i * spacing[0], j * spacing[1], k * spacing[2]).
+ *   - A contour handle keeps a reference to its volume; destroy contours before
+ *     their volume.
+ *   - A CUDA device (the current one) is required; there is no CPU path.
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AC_OK = 0,
+    AC_ERR_ARG = 1,      /* invalid argument (null pointer, bad size, bad enum)      */
+    AC_ERR_OOM = 2,      /* a device or pinned allocation failed                      */
+    AC_ERR_CUDA = 3,     /* a CUDA runtime/driver call or a kernel launch failed      */
+    AC_ERR_STATE = 4,    /* handle in the wrong state (e.g. no contours evolved)     */
+    AC_ERR_TIMEOUT = 5,  /* a bounded device wait gave up (status word set)           */
+    AC_ERR_BUDGET = 6,   /* request larger than the configured memory budget          */
+    AC_ERR_NUMERIC = 7   /* non-finite contour state detected (status word set)       */
+} ac_status;
+
+typedef enum { AC_U8 = 0, AC_U16 = 1, AC_F16 = 2, AC_F32 = 3 } ac_dtype;
+
+typedef enum {
+    AC_PATH_BRICK = 0,   /* bricks + halo staged in shared memory by 3D TMA, one
+                            persistent pass over all T iterations (default)        */
+    AC_PATH_PLAIN = 1    /* one launch per iteration, gathers from global memory    */
+} ac_path;
+
+typedef struct ac_volume ac_volume;
+typedef struct ac_contours ac_contours;
+
+/* ------------------------------------------------------------------ volume ---- */
+/*
+ * ac_create_volume -- copy an image into device memory (stage a1).
+ * The image I(x) of Eqs. 1-2 / 5: `dims` = (nx, ny, nz) voxels, x fastest; ndim 2
+ * ignores nz (use 1).  Every used dimension must be >= 2.  `data` holds the voxels
+ * with element strides (1, row_stride, plane_stride); pass row_stride = 0 /
+ * plane_stride = 0 for a dense array.  `data_on_device` = 0: `data` is host memory
+ * (pinned memory gives an asynchronous copy), 1: device memory of the current
+ * device.  The library keeps its own copy in a row-pitched layout (row pitch a
+ * multiple of 16 bytes, as TMA requires); `data` may be reused once the stream has
+ * passed this call.  Intensity used by the method = intensity_scale * stored value
+ * (AC_F16 stores IEEE binary16).  spacing: physical voxel size per axis (> 0).
+ * Errors: AC_ERR_ARG on bad sizes/dtype/null, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+ac_status ac_create_volume(const void *data, int data_on_device, ac_dtype dtype, int ndim,
+                           const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
+                           const float spacing[3], float intensity_scale, void *cuda_stream,
+                           ac_volume **out);
+void ac_destroy_volume(ac_volume *vol);
+
+/*
+ * ac_load_volume -- copy new voxels of the same extents and type into an existing
+ * volume (a new image tile replacing the old one; no allocation).  Arguments as
+ * ac_create_volume.  Asynchronous.  Errors: AC_ERR_ARG, AC_ERR_CUDA.
+ */
+ac_status ac_load_volume(ac_volume *vol, const void *data, int data_on_device, int64_t row_stride,
+                         int64_t plane_stride, void *cuda_stream);
+
+/* ------------------------------------------------------------------ seeding --- */
+/*
+ * Seeding (stage a2).  Lattice: the volume box is tiled by cells of side `stride`
+ * (physical units; figures 1b and 4b place neighbours sqrt(1.5) R apart, so
+ * R0 = stride / sqrt(1.5) when R0 <= 0), one contour at each cell centre, the
+ * leftover split evenly between both ends of each axis; contour index k runs x
+ * fastest.  Explicit: `explicit_cR` (host, n_explicit rows of cx, cy, cz, R as
+ * float32) places contour k at row k; centres are clamped into the box of voxel
+ * centres and radii must lie in (0, 1e6].  The contour index k enters the Philox
+ * counter, so results do not depend on how contours are scheduled.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+typedef struct {
+    double stride;   /* lattice stride, physical units; ignored when n_explicit > 0 */
+    double R0;       /* initial radius; <= 0 selects stride / sqrt(1.5)            */
+} ac_seed_params;
+
+ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const float *explicit_cR,
+                  int64_t n_explicit, void *cuda_stream, ac_contours **out);
+int64_t ac_contour_count(const ac_contours *ctr);
+void ac_destroy_contours(ac_contours *ctr);
+
+/* ac_reseed -- write the lattice of a lattice-seeded handle again (same stride and
+ * R0, energies zero) and clear its status word; no allocation.  Asynchronous.
+ * Errors: AC_ERR_ARG, AC_ERR_STATE (handle seeded explicitly), AC_ERR_CUDA. */
+ac_status ac_reseed(ac_contours *ctr, void *cuda_stream);
+
+/* ------------------------------------------------------------------ evolution - */
+/*
+ * ac_evolve -- T iterations of Monte-Carlo gradient descent for every contour
+ * (stages a3-a8).  Iteration n, for contour k at centre c and radius R:
+ *   samples  x_j = c + (R + dR/2) u_j, j < N, u_j uniform in the unit ball (disk)
+ *            from Philox4x32-10(counter = (j, n, k, stream_id) [2D: (j/2, ...)],
+ *            key = (seed low 32 bits, seed high 32 bits)) -- "Monte-Carlo
+ *            Integration" section;
+ *   sums     J = V/N sum S I, J_R = V/N sum dS/dR I, J_c = V/N sum S'(r)(-(x-c)/r) I
+ *            with V the volume (area) of the ball and S the four-region weight of
+ *            Eq. 5 (linear bands of widths dR and dR / 2^(1/d));
+ *   energy   E = J / (2R)^d (Eqs. 5-6), dE/dR = (-d J / R + J_R) / (2R)^d,
+ *            dE/dc = J_c / (2R)^d (Eqs. 7-11 in centre/radius form);
+ *   update   c -= eps_n/2 dE/dc, R -= eps_n/2 dE/dR, eps_n = eps0/sqrt(n)
+ *            (Eqs. 12-15), each step clamped to max_step, R to [Rmin, Rmax] and c
+ *            to the box of voxel centres.
+ * Iterations run from n = first_iter to first_iter + T - 1; the update after the
+ * last one is applied only when update_last is set.  Afterwards each contour holds
+ * its centre and radius and the energy of its last evaluation.  Arithmetic is
+ * FP32 with compensated sums; volumes are read as stored (uint8/uint16/FP16/FP32).  `trace` (optional) records the state
+ * and results of every evaluation for contours k in [k_begin, k_end) and
+ * iterations n in [t_begin, t_end).  Asynchronous on the stream.
+ * Errors: AC_ERR_ARG (bad parameters, trace too small), AC_ERR_OOM, AC_ERR_CUDA.
+ * Bounded device waits that give up set the handle's status word, reported as
+ * AC_ERR_TIMEOUT by the next synchronizing call.
+ */
+typedef struct {
+    int32_t N;                 /* MC samples per contour and iteration (>= 1)         */
+    int32_t T;                 /* iterations (>= 1)                                  */
+    float eps0;                /* learning-rate constant, eps_n = eps0 / sqrt(n)      */
+    float dR;                  /* fixed band width dR (> 0), physical units           */
+    float Rmin, Rmax;          /* radius clamp, 0 < Rmin <= Rmax                      */
+    float max_step;            /* per-iteration step clamp (> 0)                      */
+    uint64_t seed;             /* Philox key                                          */
+    uint32_t stream_id;        /* fourth Philox counter word                          */
+    int32_t path;              /* ac_path                                             */
+    int32_t lanes_per_contour; /* 8, 16 or 32 lanes cooperate on one contour; 0=auto  */
+    int32_t compensated;       /* 1: compensated (Kahan + TwoSum) sums, 0: plain FP32 */
+    int32_t brick[3];          /* brick interior in voxels per axis; 0 = auto          */
+    int32_t warps_per_block;   /* 0 = auto                                            */
+    int32_t first_iter;        /* iteration number n of the first iteration (0 -> 1)  */
+    int32_t update_last;       /* 1: also update after the last evaluation (a run
+                                  continued by a later call with first_iter =
+                                  first_iter + T then equals one uninterrupted run)   */
+} ac_evolve_params;
+
+typedef struct {
+    float *device_buf;  /* (t_end - t_begin) x (k_end - k_begin) x 9 floats, device:
+                           cx, cy, cz, R, E, dE/dR, dE/dcx, dE/dcy, dE/dcz          */
+    int64_t k_begin, k_end;
+    int32_t t_begin, t_end; /* 1-based iterations, t_end exclusive                  */
+} ac_trace;
+
+ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_trace *trace,
+                    void *cuda_stream);
+
+/*
+ * ac_evolve_batch -- one launch over several contour sets, each on its own volume
+ * (the batching form: uneven volumes and contour counts in one persistent pass).
+ * params are shared; each set keeps its own Philox key in seeds[i] so results match
+ * ac_evolve on that set alone.  Asynchronous.  Errors as ac_evolve.
+ */
+ac_status ac_evolve_batch(ac_contours *const *sets, const uint64_t *seeds, int32_t n_sets,
+                          const ac_evolve_params *params, void *cuda_stream);
+
+/* ------------------------------------------------------------------ localize -- */
+/*
+ * ac_localize -- energy cull and overlap competition (stage a9, section "Results
+ * and Discussion"): contours with E > E0 or non-finite E are removed; the rest are
+ * visited in order of increasing (E, k) and a contour is kept unless a kept one
+ * overlaps it, overlap meaning |c' - c''| < rho_d max(R', R''), rho_3 = 2^(-1/3),
+ * rho_2 = 2^(-1/2).  Writes up to `cap` cells (host memory) in acceptance order and
+ * the total count to *n_out (which may exceed cap).  Cell radius = rho_d R.
+ * Synchronizes the stream.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA,
+ * AC_ERR_TIMEOUT / AC_ERR_NUMERIC when the status word is set.
+ */
+typedef struct {
+    float E0;           /* energy threshold */
+} ac_localize_params;
+
+typedef struct {
+    float c[3];         /* centre, physical */
+    float r;            /* rho_d * R        */
+    float E;            /* energy           */
+    int32_t id;         /* contour index k  */
+} ac_cell;
+
+ac_status ac_localize(ac_contours *ctr, const ac_localize_params *params, ac_cell *out_host,
+                      int64_t cap, int64_t *n_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------ state ----- */
+/*
+ * ac_get_state / ac_set_state -- copy the contour state to / from host memory as
+ * 5 x C float32, structure of arrays: cx[C], cy[C], cz[C], R[C], E[C].  With the
+ * counter-based generator, setting a saved state and evolving from iteration n
+ * reproduces an uninterrupted run (see first_iter / update_last).  ac_set_state
+ * clamps centres into the box of voxel centres and needs radii in (0, 1e6];
+ * ac_get_state synchronizes the stream and
+ * reports the status word.  Errors: AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_TIMEOUT,
+ * AC_ERR_NUMERIC.
+ */
+ac_status ac_get_state(ac_contours *ctr, float *out_host, void *cuda_stream);
+ac_status ac_set_state(ac_contours *ctr, const float *in_host, void *cuda_stream);
+/* Device pointer to the same 5 x C float32 state (valid until the handle dies). */
+ac_status ac_state_device_ptr(ac_contours *ctr, float **out);
+
+/* ------------------------------------------------------------------ support --- */
+/* Philox4x32-10 words for n counters (device buffers of 4 x n uint32, x fastest),
+ * computed by the same device routine that draws the samples.  Asynchronous. */
+ac_status ac_philox4x32_10(const uint32_t *ctr_dev, uint64_t key, uint32_t *out_dev, int64_t n,
+                           void *cuda_stream);
+
+/* Device time in milliseconds of the evolution kernel launch(es) of the last
+ * ac_evolve / ac_evolve_batch on this handle (CUDA events recorded by the library
+ * on the launching stream; binning and sorting excluded).  Synchronizes on the end
+ * event.  Errors: AC_ERR_ARG, AC_ERR_STATE (nothing evolved yet), AC_ERR_CUDA. */
+ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms);
+
+/* Number of the library's own kernel launches since it was loaded (all threads).
+ * Sorting and selection steps run CUB library kernels, which are not counted. */
+int64_t ac_kernel_launches(void);
+
+/* Message for the last failure on this thread ("" if none). */
+const char *ac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AC_H */

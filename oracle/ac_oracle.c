@@ -564,3 +564,17 @@ void or_unit_samples(const or_params *P, int64_t iter, int64_t k, double *out)
         }
     }
 }
+
+/* Teacher-forced evaluation of many (state, iteration, contour) triples: rows of
+ * `cR` are (cx, cy, cz, R), `iters` and `ks` give n and k; writes OR_RES_LEN doubles
+ * per row.  Independent rows are spread over `nthreads` OpenMP threads. */
+void or_eval_many(const or_image *img, const or_params *P, int64_t m, const double *cR, const int64_t *iters,
+                  const int64_t *ks, double *res, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < m; ++i)
+        or_eval_cr(img, P, cR + 4 * i, cR[4 * i + 3], iters[i], ks[i], res + (int64_t)OR_RES_LEN * i);
+}

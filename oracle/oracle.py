@@ -92,6 +92,7 @@ def lib():
                 "or_seed_lattice": (ct.c_int64, [ct.c_int, I64, D, ct.c_double, D]),
                 "or_localize": (ct.c_int64, [ct.c_int, ct.c_int64, D, D, ct.c_double, I64]),
                 "or_unit_samples": (None, [PP, ct.c_int64, ct.c_int64, D]),
+                "or_eval_many": (None, [IP, PP, ct.c_int64, D, I64, I64, D, ct.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(l, name)
@@ -207,6 +208,19 @@ def eval_cr(img, params, c, R, it, k) -> np.ndarray:
     c = np.ascontiguousarray(list(c) + [0.0] * (3 - len(c)), dtype=np.float64)
     res = np.empty(RES_LEN)
     lib().or_eval_cr(ct.byref(img.s), ct.byref(params), _P(c, ct.c_double), float(R), it, k, _P(res, ct.c_double))
+    return res
+
+
+def eval_many(img, params, cR, iters, ks, nthreads: int = 0) -> np.ndarray:
+    """Teacher-forced evaluations: rows (cx, cy, cz, R) at iterations ``iters`` for
+    contour indices ``ks``; returns (m, RES_LEN)."""
+    cR = np.ascontiguousarray(cR, dtype=np.float64).reshape(-1, 4)
+    m = len(cR)
+    it = np.ascontiguousarray(np.broadcast_to(np.asarray(iters, dtype=np.int64), (m,)))
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(ks, dtype=np.int64), (m,)))
+    res = np.empty((m, RES_LEN))
+    lib().or_eval_many(ct.byref(img.s), ct.byref(params), m, _P(cR, ct.c_double), _P(it, ct.c_int64),
+                       _P(kk, ct.c_int64), _P(res, ct.c_double), nthreads)
     return res
 
 

@@ -1,0 +1,357 @@
+"""Thin ctypes binding of libac (include/ac.h), with the C ABI's names.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Importing this module loads (and, if needed, builds) ``libac.so``; when the
+library cannot be built or loaded the import fails loudly -- there is no CPU
+path.  Arrays may be numpy (host) or torch tensors (host or CUDA).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import dataclasses
+import math
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+AC_OK, AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STATE, AC_ERR_TIMEOUT, AC_ERR_BUDGET, AC_ERR_NUMERIC = range(8)
+AC_U8, AC_U16, AC_F16, AC_F32 = range(4)
+AC_PATH_BRICK, AC_PATH_PLAIN = 0, 1
+STATUS_NAMES = {0: "AC_OK", 1: "AC_ERR_ARG", 2: "AC_ERR_OOM", 3: "AC_ERR_CUDA", 4: "AC_ERR_STATE",
+                5: "AC_ERR_TIMEOUT", 6: "AC_ERR_BUDGET", 7: "AC_ERR_NUMERIC"}
+
+
+class ACError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ac_seed_params(ct.Structure):
+    _fields_ = [("stride", ct.c_double), ("R0", ct.c_double)]
+
+
+class ac_evolve_params(ct.Structure):
+    _fields_ = [("N", ct.c_int32), ("T", ct.c_int32), ("eps0", ct.c_float), ("dR", ct.c_float),
+                ("Rmin", ct.c_float), ("Rmax", ct.c_float), ("max_step", ct.c_float), ("seed", ct.c_uint64),
+                ("stream_id", ct.c_uint32), ("path", ct.c_int32), ("lanes_per_contour", ct.c_int32),
+                ("compensated", ct.c_int32), ("brick", ct.c_int32 * 3), ("warps_per_block", ct.c_int32),
+                ("first_iter", ct.c_int32), ("update_last", ct.c_int32)]
+
+
+class ac_trace(ct.Structure):
+    _fields_ = [("device_buf", ct.c_void_p), ("k_begin", ct.c_int64), ("k_end", ct.c_int64),
+                ("t_begin", ct.c_int32), ("t_end", ct.c_int32)]
+
+
+class ac_localize_params(ct.Structure):
+    _fields_ = [("E0", ct.c_float)]
+
+
+class ac_cell(ct.Structure):
+    _fields_ = [("c", ct.c_float * 3), ("r", ct.c_float), ("E", ct.c_float), ("id", ct.c_int32)]
+
+
+CELL_DTYPE = np.dtype([("c", np.float32, 3), ("r", np.float32), ("E", np.float32), ("id", np.int32)])
+
+_SIGS = {
+    "ac_create_volume": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_int64), ct.c_int64,
+                                    ct.c_int64, ct.POINTER(ct.c_float), ct.c_float, ct.c_void_p,
+                                    ct.POINTER(ct.c_void_p)]),
+    "ac_destroy_volume": (None, [ct.c_void_p]),
+    "ac_load_volume": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int64, ct.c_int64, ct.c_void_p]),
+    "ac_reseed": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "ac_seed": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_seed_params), ct.c_void_p, ct.c_int64, ct.c_void_p,
+                           ct.POINTER(ct.c_void_p)]),
+    "ac_contour_count": (ct.c_int64, [ct.c_void_p]),
+    "ac_destroy_contours": (None, [ct.c_void_p]),
+    "ac_evolve": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_evolve_params), ct.POINTER(ac_trace), ct.c_void_p]),
+    "ac_evolve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_uint64), ct.c_int32,
+                                   ct.POINTER(ac_evolve_params), ct.c_void_p]),
+    "ac_localize": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_localize_params), ct.c_void_p, ct.c_int64,
+                               ct.POINTER(ct.c_int64), ct.c_void_p]),
+    "ac_get_state": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "ac_set_state": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "ac_state_device_ptr": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "ac_philox4x32_10": (ct.c_int, [ct.c_void_p, ct.c_uint64, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+    "ac_evolve_kernel_ms": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_float)]),
+    "ac_kernel_launches": (ct.c_int64, []),
+    "ac_last_error": (ct.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if stale) and load libac.so; raises if either fails."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        l = ct.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def header_symbols() -> list:
+    """Entry points declared in include/ac.h."""
+    h = open(os.path.join(os.path.dirname(_build.HERE), "include", "ac.h")).read()
+    return sorted(set(re.findall(r"\b(ac_[a-z0-9_]+)\s*\(", h)))
+
+
+def _check(status: int):
+    if status != AC_OK:
+        raise ACError(status, load().ac_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+def _ptr(arr):
+    """(pointer, on_device, dtype code, shape, element strides) of numpy / torch data."""
+    try:
+        import torch
+        if isinstance(arr, torch.Tensor):
+            code = {torch.uint8: AC_U8, torch.int16: AC_U16, torch.float16: AC_F16, torch.float32: AC_F32}
+            if hasattr(torch, "uint16"):
+                code[torch.uint16] = AC_U16
+            return arr.data_ptr(), int(arr.is_cuda), code.get(arr.dtype), tuple(arr.shape), tuple(arr.stride())
+    except ImportError:
+        pass
+    a = np.asarray(arr)
+    code = {np.dtype(np.uint8): AC_U8, np.dtype(np.uint16): AC_U16, np.dtype(np.float16): AC_F16,
+            np.dtype(np.float32): AC_F32}.get(a.dtype)
+    return a.ctypes.data, 0, code, a.shape, tuple(s // a.itemsize for s in a.strides)
+
+
+# ------------------------------------------------------------------------ handles
+class Volume:
+    def __init__(self, handle, ndim, dims, spacing, keepalive=None):
+        self.handle = handle
+        self.ndim = ndim
+        self.dims = dims
+        self.spacing = spacing
+        self._keep = keepalive
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ac_destroy_volume(self.handle)
+            self.handle = None
+
+
+class Contours:
+    def __init__(self, handle, vol: Volume):
+        self.handle = handle
+        self.vol = vol
+
+    @property
+    def count(self) -> int:
+        return int(load().ac_contour_count(self.handle))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ac_destroy_contours(self.handle)
+            self.handle = None
+
+
+# ------------------------------------------------------------------------ entry points
+def ac_create_volume(data, spacing=(1.0, 1.0, 1.0), intensity_scale: float = 1.0, stream=None,
+                     dtype: int | None = None) -> Volume:
+    """``data`` indexed [z, y, x] (3D) or [y, x] (2D), x fastest."""
+    l = load()
+    ptr, on_dev, code, shape, strides = _ptr(data)
+    if dtype is not None:
+        code = dtype
+    if code is None:
+        raise ACError(AC_ERR_ARG, "unsupported element type")
+    ndim = len(shape)
+    if ndim not in (2, 3) or strides[-1] != 1:
+        raise ACError(AC_ERR_ARG, "need a 2D or 3D array with unit x stride")
+    dims = (ct.c_int64 * 3)(*(list(shape[::-1]) + [1] * (3 - ndim)))
+    row = strides[-2]
+    plane = strides[-3] if ndim == 3 else 0
+    sp = (ct.c_float * 3)(*[float(s) for s in (list(spacing) + [1.0] * 3)[:3]])
+    out = ct.c_void_p()
+    _check(l.ac_create_volume(ct.c_void_p(ptr), on_dev, code, ndim, dims, row, plane, sp, intensity_scale,
+                              ct.c_void_p(_stream(stream)), ct.byref(out)))
+    return Volume(out, ndim, tuple(dims), tuple(sp), keepalive=data)
+
+
+def ac_load_volume(vol: Volume, data, stream=None):
+    """New voxels (same extents and type) into an existing volume."""
+    ptr, on_dev, code, shape, strides = _ptr(data)
+    if tuple(shape[::-1]) != tuple(vol.dims[:len(shape)]):
+        raise ACError(AC_ERR_ARG, "extents differ from the volume's")
+    row = strides[-2]
+    plane = strides[-3] if len(shape) == 3 else 0
+    _check(load().ac_load_volume(vol.handle, ct.c_void_p(ptr), on_dev, row, plane, ct.c_void_p(_stream(stream))))
+    vol._keep = data
+
+
+def ac_reseed(ctr: Contours, stream=None):
+    _check(load().ac_reseed(ctr.handle, ct.c_void_p(_stream(stream))))
+
+
+def ac_destroy_volume(vol: Volume):
+    if vol.handle:
+        load().ac_destroy_volume(vol.handle)
+        vol.handle = None
+
+
+def ac_seed(vol: Volume, stride: float | None = None, R0: float = 0.0, explicit=None, stream=None) -> Contours:
+    l = load()
+    p = ac_seed_params(float(stride or 0.0), float(R0))
+    out = ct.c_void_p()
+    if explicit is not None:
+        e = np.ascontiguousarray(explicit, dtype=np.float32).reshape(-1, 4)
+        _check(l.ac_seed(vol.handle, ct.byref(p), ct.c_void_p(e.ctypes.data), len(e), ct.c_void_p(_stream(stream)),
+                         ct.byref(out)))
+    else:
+        _check(l.ac_seed(vol.handle, ct.byref(p), None, 0, ct.c_void_p(_stream(stream)), ct.byref(out)))
+    return Contours(out, vol)
+
+
+def ac_contour_count(ctr: Contours) -> int:
+    return int(load().ac_contour_count(ctr.handle))
+
+
+def ac_destroy_contours(ctr: Contours):
+    if ctr.handle:
+        load().ac_destroy_contours(ctr.handle)
+        ctr.handle = None
+
+
+@dataclasses.dataclass
+class EvolveParams:
+    N: int
+    T: int
+    eps0: float
+    dR: float = 1.0
+    Rmin: float = 0.5
+    Rmax: float = 1e6
+    max_step: float = 0.5
+    seed: int = 0
+    stream_id: int = 0
+    path: int = AC_PATH_BRICK
+    lanes_per_contour: int = 0
+    compensated: int = 1
+    brick: tuple = (0, 0, 0)
+    warps_per_block: int = 0
+    first_iter: int = 0
+    update_last: int = 0
+
+    def to_c(self) -> ac_evolve_params:
+        p = ac_evolve_params()
+        for f in dataclasses.fields(self):
+            if f.name == "brick":
+                p.brick[:] = tuple(int(b) for b in self.brick)
+            else:
+                setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def default_params(ndim: int, R0: float, contrast: float, N: int, T: int, seed: int = 0, **kw) -> EvolveParams:
+    """Defaults for the values the paper leaves open: eps0 = 8 R0^2 / A (A = the
+    expected foreground-background contrast in scaled intensity), dR = 1,
+    Rmin = max(dR/2, R0/2), Rmax = 3 R0, max_step = 0.5."""
+    dR = kw.pop("dR", 1.0)
+    return EvolveParams(N=N, T=T, eps0=8.0 * R0 * R0 / contrast, dR=dR, Rmin=max(0.5 * dR, 0.5 * R0), Rmax=3.0 * R0,
+                        seed=seed, **kw)
+
+
+def default_E0(ndim: int, contrast: float) -> float:
+    """Half the ideal-blob minimum energy (-A pi/12 in 3D, -A pi/8 in 2D)."""
+    return -math.pi * contrast / 24.0 if ndim == 3 else -math.pi * contrast / 16.0
+
+
+def ac_evolve(ctr: Contours, params: EvolveParams, trace=None, stream=None):
+    """``trace``: None or (device tensor, k_begin, k_end, t_begin, t_end)."""
+    l = load()
+    p = params.to_c()
+    tr = None
+    if trace is not None:
+        buf, k0, k1, t0, t1 = trace
+        need = (t1 - t0) * (k1 - k0) * 9
+        if buf.numel() < need or not buf.is_cuda or buf.dtype.itemsize != 4:
+            raise ACError(AC_ERR_ARG, "trace buffer too small or not a float32 CUDA tensor")
+        tr = ac_trace(buf.data_ptr(), k0, k1, t0, t1)
+    _check(l.ac_evolve(ctr.handle, ct.byref(p), ct.byref(tr) if tr is not None else None,
+                       ct.c_void_p(_stream(stream))))
+
+
+def ac_evolve_batch(sets, params: EvolveParams, seeds=None, stream=None):
+    l = load()
+    p = params.to_c()
+    arr = (ct.c_void_p * len(sets))(*[s.handle.value if isinstance(s.handle, ct.c_void_p) else s.handle for s in sets])
+    sd = None
+    if seeds is not None:
+        sd = (ct.c_uint64 * len(sets))(*[int(s) for s in seeds])
+    _check(l.ac_evolve_batch(arr, sd, len(sets), ct.byref(p), ct.c_void_p(_stream(stream))))
+
+
+def ac_localize(ctr: Contours, E0: float, cap: int | None = None, stream=None) -> np.ndarray:
+    l = load()
+    cap = ctr.count if cap is None else cap
+    out = np.zeros(max(cap, 1), dtype=CELL_DTYPE)
+    n = ct.c_int64()
+    _check(l.ac_localize(ctr.handle, ct.byref(ac_localize_params(E0)), ct.c_void_p(out.ctypes.data), cap,
+                         ct.byref(n), ct.c_void_p(_stream(stream))))
+    return out[:min(n.value, cap)]
+
+
+def ac_get_state(ctr: Contours, stream=None) -> np.ndarray:
+    """(5, C) float32: cx, cy, cz, R, E."""
+    l = load()
+    out = np.empty((5, ctr.count), dtype=np.float32)
+    _check(l.ac_get_state(ctr.handle, ct.c_void_p(out.ctypes.data), ct.c_void_p(_stream(stream))))
+    return out
+
+
+def ac_set_state(ctr: Contours, state: np.ndarray, stream=None):
+    l = load()
+    s = np.ascontiguousarray(state, dtype=np.float32).reshape(5, -1)
+    _check(l.ac_set_state(ctr.handle, ct.c_void_p(s.ctypes.data), ct.c_void_p(_stream(stream))))
+
+
+def ac_state_device_ptr(ctr: Contours) -> int:
+    out = ct.c_void_p()
+    _check(load().ac_state_device_ptr(ctr.handle, ct.byref(out)))
+    return out.value
+
+
+def ac_philox4x32_10(ctr_dev, key: int, stream=None):
+    """``ctr_dev``: CUDA int32/uint32 tensor of shape (n, 4); returns words likewise."""
+    import torch
+    out = torch.empty_like(ctr_dev)
+    _check(load().ac_philox4x32_10(ct.c_void_p(ctr_dev.data_ptr()), key, ct.c_void_p(out.data_ptr()),
+                                   ctr_dev.shape[0], ct.c_void_p(_stream(stream))))
+    return out
+
+
+def ac_evolve_kernel_ms(ctr: Contours) -> float:
+    ms = ct.c_float()
+    _check(load().ac_evolve_kernel_ms(ctr.handle, ct.byref(ms)))
+    return float(ms.value)
+
+
+def ac_kernel_launches() -> int:
+    return int(load().ac_kernel_launches())
+
+
+def ac_last_error() -> str:
+    return load().ac_last_error().decode()

@@ -1,0 +1,742 @@
+// ac_api.cu -- C ABI of libac: volumes, seeding, evolution orchestration, state.
+// Method: Lotfollahi et al., arXiv:1804.06304 (see include/ac.h for the mapping of
+// each entry point to the paper).
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <cub/cub.cuh>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ac_host.h"
+
+namespace ac {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void Scratch::release_all()
+{
+    DevBuf *all[] = {&keys, &vals, &skeys, &svals, &cub, &desc, &tmaps, &flags, &surv, &ekeys, &surv_sorted,
+                     &pos, &cellk, &celli, &cellk_s, &celli_s, &cell_start, &stat, &acc, &cells, &counters};
+    for (DevBuf *b : all) b->release();
+}
+
+}  // namespace ac
+
+#define AC_FAIL(code, msg)        \
+    do {                          \
+        ac::set_error(msg);       \
+        return code;              \
+    } while (0)
+
+#define AC_CUDA(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            ac::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+            return e_ == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;                          \
+        }                                                                                               \
+    } while (0)
+
+using namespace ac;
+
+static int elem_size(ac_dtype t)
+{
+    switch (t) {
+    case AC_U8: return 1;
+    case AC_U16: return 2;
+    case AC_F16: return 2;
+    case AC_F32: return 4;
+    }
+    return 0;
+}
+
+extern "C" const char *ac_last_error(void) { return g_err.c_str(); }
+
+extern "C" int64_t ac_kernel_launches(void) { return g_launches.load(); }
+
+// Clamp a centre coordinate into the box of voxel centres of one axis.
+static float clamp_box(float c, const ac_volume *v, int d)
+{
+    const float hi = (float)((double)(v->n[d] - 1) * v->sp[d]);
+    return c < 0.0f ? 0.0f : (c > hi ? hi : c);
+}
+
+// Copy voxels with element strides (1, row_stride, plane_stride) into the
+// row-pitched device copy of `v`.
+static cudaError_t copy_voxels(const ac_volume *v, const void *data, int data_on_device, int64_t row_stride,
+                               int64_t plane_stride, cudaStream_t st)
+{
+    const int64_t *n = v->n;
+    const int es = v->es;
+    const size_t row_bytes = (size_t)n[0] * es;
+    const size_t pitch = (size_t)v->pitch_y * es;
+    const cudaMemcpyKind kind = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const char *src = (const char *)data;
+    if (pitch == row_bytes && row_stride == n[0] && plane_stride == row_stride * n[1])
+        return cudaMemcpyAsync(v->data, src, v->bytes, kind, st);
+    if (plane_stride == row_stride * n[1])
+        return cudaMemcpy2DAsync(v->data, pitch, src, (size_t)row_stride * es, row_bytes, (size_t)(n[1] * n[2]), kind, st);
+    cudaError_t e = cudaSuccess;
+    for (int64_t z = 0; z < n[2] && e == cudaSuccess; ++z)
+        e = cudaMemcpy2DAsync((char *)v->data + z * pitch * n[1], pitch, src + z * plane_stride * es,
+                              (size_t)row_stride * es, row_bytes, (size_t)n[1], kind, st);
+    return e;
+}
+
+// ------------------------------------------------------------------ volume
+extern "C" ac_status ac_create_volume(const void *data, int data_on_device, ac_dtype dtype, int ndim,
+                                      const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
+                                      const float spacing[3], float intensity_scale, void *cuda_stream,
+                                      ac_volume **out)
+{
+    g_err.clear();
+    if (!out) AC_FAIL(AC_ERR_ARG, "ac_create_volume: out is NULL");
+    *out = nullptr;
+    if (!data || !dims || !spacing) AC_FAIL(AC_ERR_ARG, "ac_create_volume: NULL data, dims or spacing");
+    const int es = elem_size(dtype);
+    if (es == 0) AC_FAIL(AC_ERR_ARG, "ac_create_volume: unknown dtype");
+    if (ndim != 2 && ndim != 3) AC_FAIL(AC_ERR_ARG, "ac_create_volume: ndim must be 2 or 3");
+    int64_t n[3] = {dims[0], dims[1], ndim == 3 ? dims[2] : 1};
+    for (int d = 0; d < ndim; ++d) {
+        if (n[d] < 2 || n[d] > (1 << 30)) AC_FAIL(AC_ERR_ARG, "ac_create_volume: every used dimension must be in [2, 2^30]");
+        if (!(spacing[d] > 0.0f) || !std::isfinite(spacing[d]))
+            AC_FAIL(AC_ERR_ARG, "ac_create_volume: spacing must be positive and finite");
+    }
+    if (!std::isfinite(intensity_scale)) AC_FAIL(AC_ERR_ARG, "ac_create_volume: intensity_scale not finite");
+    if (row_stride == 0) row_stride = n[0];
+    if (plane_stride == 0) plane_stride = row_stride * n[1];
+    if (row_stride < n[0] || plane_stride < row_stride * n[1])
+        AC_FAIL(AC_ERR_ARG, "ac_create_volume: strides smaller than the extents");
+    if (n[0] * n[1] * n[2] > ((int64_t)1 << 36)) AC_FAIL(AC_ERR_ARG, "ac_create_volume: volume too large");
+
+    ac_volume *v = new ac_volume();
+    cudaGetDevice(&v->device);
+    v->dtype = dtype;
+    v->ndim = ndim;
+    for (int d = 0; d < 3; ++d) {
+        v->n[d] = n[d];
+        v->sp[d] = d < ndim ? spacing[d] : 1.0f;
+    }
+    v->scale = intensity_scale;
+    v->es = es;
+    const size_t row_bytes = (size_t)n[0] * es;
+    const size_t pitch = (row_bytes + 15) / 16 * 16;   // TMA: strides multiple of 16 bytes
+    v->pitch_y = (int64_t)(pitch / es);
+    v->pitch_z = v->pitch_y * n[1];
+    v->bytes = pitch * (size_t)n[1] * (size_t)n[2];
+    cudaError_t e = cudaMalloc(&v->data, v->bytes);
+    if (e != cudaSuccess) {
+        delete v;
+        AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
+                std::string("ac_create_volume: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    e = copy_voxels(v, data, data_on_device, row_stride, plane_stride, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        cudaFree(v->data);
+        delete v;
+        AC_FAIL(AC_ERR_CUDA, std::string("ac_create_volume: copy: ") + cudaGetErrorString(e));
+    }
+    *out = v;
+    return AC_OK;
+}
+
+extern "C" ac_status ac_load_volume(ac_volume *vol, const void *data, int data_on_device, int64_t row_stride,
+                                    int64_t plane_stride, void *cuda_stream)
+{
+    g_err.clear();
+    if (!vol || !data) AC_FAIL(AC_ERR_ARG, "ac_load_volume: NULL argument");
+    if (row_stride == 0) row_stride = vol->n[0];
+    if (plane_stride == 0) plane_stride = row_stride * vol->n[1];
+    if (row_stride < vol->n[0] || plane_stride < row_stride * vol->n[1])
+        AC_FAIL(AC_ERR_ARG, "ac_load_volume: strides smaller than the extents");
+    AC_CUDA(copy_voxels(vol, data, data_on_device, row_stride, plane_stride, (cudaStream_t)cuda_stream));
+    return AC_OK;
+}
+
+extern "C" void ac_destroy_volume(ac_volume *vol)
+{
+    if (!vol) return;
+    cudaFree(vol->data);
+    delete vol;
+}
+
+// ------------------------------------------------------------------ seeding
+__global__ void seed_lattice_kernel(float *state, int64_t C, int Lx, int Ly, float fx, float fy, float fz,
+                                    float stride, float R0, int ndim)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < C; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k % Lx, j = (k / Lx) % Ly, l = k / ((int64_t)Lx * Ly);
+        state[k] = fmaf((float)i, stride, fx);
+        state[C + k] = fmaf((float)j, stride, fy);
+        state[2 * C + k] = ndim == 3 ? fmaf((float)l, stride, fz) : 0.0f;
+        state[3 * C + k] = R0;
+        state[4 * C + k] = 0.0f;
+    }
+}
+
+static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out)
+{
+    ac_contours *c = new ac_contours();
+    c->vol = vol;
+    c->C = C;
+    cudaError_t e = cudaMalloc(&c->state, sizeof(float) * 5 * (size_t)(C > 0 ? C : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int32_t) * 4);
+    if (e != cudaSuccess) {
+        if (c->state) cudaFree(c->state);
+        delete c;
+        AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
+                std::string("ac_seed: allocation: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return AC_OK;
+}
+
+extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const float *explicit_cR,
+                             int64_t n_explicit, void *cuda_stream, ac_contours **out)
+{
+    g_err.clear();
+    if (!out) AC_FAIL(AC_ERR_ARG, "ac_seed: out is NULL");
+    *out = nullptr;
+    if (!vol) AC_FAIL(AC_ERR_ARG, "ac_seed: vol is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (n_explicit > 0) {
+        if (!explicit_cR) AC_FAIL(AC_ERR_ARG, "ac_seed: explicit_cR is NULL");
+        if (n_explicit >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_seed: too many contours");
+        std::vector<float> soa((size_t)n_explicit * 5, 0.0f);
+        double rmax = 0.0;
+        for (int64_t k = 0; k < n_explicit; ++k) {
+            for (int m = 0; m < 4; ++m) {
+                const float x = explicit_cR[4 * k + m];
+                if (!std::isfinite(x)) AC_FAIL(AC_ERR_ARG, "ac_seed: non-finite explicit seed");
+                soa[(size_t)m * n_explicit + k] = x;
+            }
+            if (!(explicit_cR[4 * k + 3] > 0.0f) || explicit_cR[4 * k + 3] > 1e6f)
+                AC_FAIL(AC_ERR_ARG, "ac_seed: explicit radius must be in (0, 1e6]");
+            for (int d = 0; d < vol->ndim; ++d)
+                soa[(size_t)d * n_explicit + k] = clamp_box(soa[(size_t)d * n_explicit + k], vol, d);
+            if (vol->ndim == 2) soa[(size_t)2 * n_explicit + k] = 0.0f;
+            rmax = std::max(rmax, (double)explicit_cR[4 * k + 3]);
+        }
+        ac_contours *c = nullptr;
+        ac_status s = make_contours(vol, n_explicit, &c);
+        if (s != AC_OK) return s;
+        cudaError_t e = cudaMemcpy(c->state, soa.data(), soa.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            ac_destroy_contours(c);
+            AC_FAIL(AC_ERR_CUDA, std::string("ac_seed: copy: ") + cudaGetErrorString(e));
+        }
+        c->r_hint = rmax;
+        c->stride_hint = std::sqrt(1.5) * rmax;
+        *out = c;
+        return AC_OK;
+    }
+    if (!params) AC_FAIL(AC_ERR_ARG, "ac_seed: params is NULL");
+    const double s = params->stride;
+    if (!(s > 0.0) || !std::isfinite(s)) AC_FAIL(AC_ERR_ARG, "ac_seed: stride must be positive");
+    const double R0 = params->R0 > 0.0 ? params->R0 : s / std::sqrt(1.5);
+    int64_t L[3] = {1, 1, 1};
+    double first[3] = {0, 0, 0};
+    for (int d = 0; d < vol->ndim; ++d) {
+        const double ext = (double)vol->n[d] * vol->sp[d];
+        L[d] = (int64_t)std::floor(ext / s);
+        if (L[d] < 1) L[d] = 1;
+        first[d] = -0.5 * vol->sp[d] + 0.5 * (ext - (double)L[d] * s) + 0.5 * s;
+    }
+    const int64_t C = L[0] * L[1] * L[2];
+    if (C >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_seed: lattice too fine");
+    ac_contours *c = nullptr;
+    ac_status rs = make_contours(vol, C, &c);
+    if (rs != AC_OK) return rs;
+    c->lattice = true;
+    for (int d = 0; d < 3; ++d) {
+        c->L[d] = L[d];
+        c->first[d] = (float)first[d];
+    }
+    c->stride = (float)s;
+    c->R0 = (float)R0;
+    c->r_hint = R0;
+    c->stride_hint = s;
+    ac_status rs2 = ac_reseed(c, cuda_stream);
+    if (rs2 != AC_OK) {
+        ac_destroy_contours(c);
+        return rs2;
+    }
+    *out = c;
+    return AC_OK;
+}
+
+extern "C" ac_status ac_reseed(ac_contours *c, void *cuda_stream)
+{
+    if (!c) AC_FAIL(AC_ERR_ARG, "ac_reseed: NULL handle");
+    if (!c->lattice) AC_FAIL(AC_ERR_STATE, "ac_reseed: handle was seeded explicitly");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int threads = 256;
+    const int64_t C = c->C;
+    const int64_t blocks = std::min<int64_t>((C + threads - 1) / threads, 1 << 16);
+    AC_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int32_t) * 4, st));
+    seed_lattice_kernel<<<(unsigned)blocks, threads, 0, st>>>(c->state, C, (int)c->L[0], (int)c->L[1], c->first[0],
+                                                              c->first[1], c->first[2], c->stride, c->R0,
+                                                              c->vol->ndim);
+    count_launch();
+    AC_CUDA(cudaGetLastError());
+    return AC_OK;
+}
+
+extern "C" int64_t ac_contour_count(const ac_contours *ctr) { return ctr ? ctr->C : -1; }
+
+extern "C" void ac_destroy_contours(ac_contours *ctr)
+{
+    if (!ctr) return;
+    ctr->scratch.release_all();
+    if (ctr->ev0) cudaEventDestroy(ctr->ev0);
+    if (ctr->ev1) cudaEventDestroy(ctr->ev1);
+    cudaFree(ctr->state);
+    cudaFree(ctr->status);
+    delete ctr;
+}
+
+// ------------------------------------------------------------------ state
+static ac_status check_status(ac_contours *ctr, cudaStream_t st)
+{
+    int32_t s[4];
+    AC_CUDA(cudaMemcpyAsync(s, ctr->status, sizeof(s), cudaMemcpyDeviceToHost, st));
+    AC_CUDA(cudaStreamSynchronize(st));
+    if (s[0] & STATUS_TMA_TIMEOUT) AC_FAIL(AC_ERR_TIMEOUT, "device status: a brick load did not complete in time");
+    if (s[0] & STATUS_LOCALIZE_LIMIT) AC_FAIL(AC_ERR_TIMEOUT, "device status: localization round bound reached");
+    if (s[0] & STATUS_NONFINITE) AC_FAIL(AC_ERR_NUMERIC, "device status: non-finite contour state");
+    return AC_OK;
+}
+
+extern "C" ac_status ac_get_state(ac_contours *ctr, float *out_host, void *cuda_stream)
+{
+    g_err.clear();
+    if (!ctr || !out_host) AC_FAIL(AC_ERR_ARG, "ac_get_state: NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    AC_CUDA(cudaMemcpyAsync(out_host, ctr->state, sizeof(float) * 5 * ctr->C, cudaMemcpyDeviceToHost, st));
+    return check_status(ctr, st);
+}
+
+extern "C" ac_status ac_set_state(ac_contours *ctr, const float *in_host, void *cuda_stream)
+{
+    g_err.clear();
+    if (!ctr || !in_host) AC_FAIL(AC_ERR_ARG, "ac_set_state: NULL argument");
+    const int64_t C = ctr->C;
+    std::vector<float> st(in_host, in_host + 5 * C);
+    for (int64_t i = 0; i < 4 * C; ++i)
+        if (!std::isfinite(st[i])) AC_FAIL(AC_ERR_ARG, "ac_set_state: non-finite centre or radius");
+    for (int64_t k = 0; k < C; ++k) {
+        if (!(st[3 * C + k] > 0.0f) || st[3 * C + k] > 1e6f) AC_FAIL(AC_ERR_ARG, "ac_set_state: radius must be in (0, 1e6]");
+        for (int d = 0; d < 3; ++d)
+            st[d * C + k] = d < ctr->vol->ndim ? clamp_box(st[d * C + k], ctr->vol, d) : 0.0f;
+    }
+    AC_CUDA(cudaMemcpyAsync(ctr->state, st.data(), sizeof(float) * 5 * C, cudaMemcpyHostToDevice,
+                            (cudaStream_t)cuda_stream));
+    AC_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    return AC_OK;
+}
+
+extern "C" ac_status ac_state_device_ptr(ac_contours *ctr, float **out)
+{
+    if (!ctr || !out) AC_FAIL(AC_ERR_ARG, "ac_state_device_ptr: NULL argument");
+    *out = ctr->state;
+    return AC_OK;
+}
+
+// ------------------------------------------------------------------ support
+__global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+        const uint4 w = philox4x32_10(c, k0, k1);
+        out[4 * i] = w.x;
+        out[4 * i + 1] = w.y;
+        out[4 * i + 2] = w.z;
+        out[4 * i + 3] = w.w;
+    }
+}
+
+extern "C" ac_status ac_philox4x32_10(const uint32_t *ctr_dev, uint64_t key, uint32_t *out_dev, int64_t n,
+                                      void *cuda_stream)
+{
+    g_err.clear();
+    if (n < 0 || (n > 0 && (!ctr_dev || !out_dev))) AC_FAIL(AC_ERR_ARG, "ac_philox4x32_10: bad arguments");
+    if (n == 0) return AC_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1 << 16);
+    philox_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)cuda_stream>>>(ctr_dev, (uint32_t)key,
+                                                                           (uint32_t)(key >> 32), out_dev, n);
+    count_launch();
+    AC_CUDA(cudaGetLastError());
+    return AC_OK;
+}
+
+// ------------------------------------------------------------------ evolution
+namespace {
+
+struct Plan {
+    int B[3], halo[3], ext[3];
+    int smem;
+    int G, warps;
+    bool brick, comp;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+ac_status check_params(const ac_evolve_params *p)
+{
+    if (!p) AC_FAIL(AC_ERR_ARG, "ac_evolve: params is NULL");
+    if (p->N < 1 || p->N > (1 << 24)) AC_FAIL(AC_ERR_ARG, "ac_evolve: N must be in [1, 2^24]");
+    if (p->T < 1 || p->T > (1 << 24)) AC_FAIL(AC_ERR_ARG, "ac_evolve: T must be in [1, 2^24]");
+    if (!(p->dR > 0.0f) || !std::isfinite(p->dR)) AC_FAIL(AC_ERR_ARG, "ac_evolve: dR must be positive");
+    if (!(p->Rmin > 0.0f) || !(p->Rmax >= p->Rmin) || !std::isfinite(p->Rmax))
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: need 0 < Rmin <= Rmax");
+    if (!(p->max_step > 0.0f) || !std::isfinite(p->max_step)) AC_FAIL(AC_ERR_ARG, "ac_evolve: max_step must be positive");
+    if (!(p->eps0 >= 0.0f) || !std::isfinite(p->eps0)) AC_FAIL(AC_ERR_ARG, "ac_evolve: eps0 must be >= 0");
+    if (p->path != AC_PATH_BRICK && p->path != AC_PATH_PLAIN) AC_FAIL(AC_ERR_ARG, "ac_evolve: unknown path");
+    if (p->first_iter < 0 || (int64_t)(p->first_iter ? p->first_iter : 1) + p->T > (1 << 30))
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: first_iter out of range");
+    if (p->lanes_per_contour != 0 && p->lanes_per_contour != 8 && p->lanes_per_contour != 16 &&
+        p->lanes_per_contour != 32)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: lanes_per_contour must be 0, 8, 16 or 32");
+    if (p->warps_per_block < 0 || p->warps_per_block > 8) AC_FAIL(AC_ERR_ARG, "ac_evolve: warps_per_block in [0, 8]");
+    for (int d = 0; d < 3; ++d)
+        if (p->brick[d] < 0 || p->brick[d] > 224) AC_FAIL(AC_ERR_ARG, "ac_evolve: brick sizes must be in [0, 224]");
+    return AC_OK;
+}
+
+// Brick interior, halo and staged-region size.  The halo covers a ball of 2.5x
+// the initial radius plus dR/2 and a margin (contours that outgrow it read from
+// global memory for that iteration).  A region starts at max(0, brick - halo)
+// (x rounded down to the 16-byte TMA alignment) and never extends past what the
+// volume needs; when the region would exceed the shared-memory budget the halo,
+// then the brick, shrinks.
+ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, const ac_evolve_params *p, Plan &pl)
+{
+    pl.brick = p->path == AC_PATH_BRICK;
+    pl.comp = p->compensated != 0;
+    pl.G = p->lanes_per_contour ? p->lanes_per_contour : 32;
+    pl.warps = p->warps_per_block ? p->warps_per_block : 8;
+    if (!pl.brick) return AC_OK;
+    const int al = 16 / vol->es;
+    const int64_t budget = 200 * 1024;
+    int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
+    for (int d = 0; d < vol->ndim; ++d) {
+        const double cells = vol->ndim == 3 ? 2.0 : 4.0;
+        B[d] = p->brick[d] ? p->brick[d] : (int)std::lround(cells * stride_hint / vol->sp[d]);
+        B[d] = std::max(1, std::min(B[d], (int)std::min<int64_t>(vol->n[d], 224)));
+        h[d] = (int)std::ceil((2.5 * r_hint + 0.5 * p->dR) / vol->sp[d]) + 2;
+    }
+    for (int iter = 0; iter < 4096; ++iter) {
+        int64_t smem = vol->es;
+        bool fits_box = true;
+        for (int d = 0; d < 3; ++d) {
+            int ext = 1;
+            if (d < vol->ndim) {
+                int64_t need = (int64_t)B[d] + 2 * (int64_t)h[d] + (d == 0 ? al - 1 : 0);
+                const int64_t cap = vol->n[d] + (d == 0 ? al - 1 : 0);
+                need = std::min(need, cap);
+                if (d == 0) need = (need + al - 1) / al * al;
+                if (need > 256) fits_box = false;
+                ext = (int)need;
+            }
+            pl.ext[d] = ext;
+            pl.B[d] = B[d];
+            pl.halo[d] = h[d];
+            smem *= ext;
+        }
+        if (fits_box && smem <= budget) {
+            pl.smem = (int)smem;
+            return AC_OK;
+        }
+        int hmax = 0, bmax = 0;
+        for (int d = 0; d < vol->ndim; ++d) {
+            hmax = std::max(hmax, h[d]);
+            bmax = std::max(bmax, B[d]);
+        }
+        if (hmax > 1) {
+            for (int d = 0; d < vol->ndim; ++d) h[d] = std::max(1, h[d] - 1);
+        } else if (bmax > 1 && p->brick[0] == 0 && p->brick[1] == 0 && p->brick[2] == 0) {
+            for (int d = 0; d < vol->ndim; ++d) B[d] = std::max(1, B[d] - 1);
+        } else {
+            break;
+        }
+    }
+    AC_FAIL(AC_ERR_ARG, "ac_evolve: staged region cannot fit the shared-memory budget; use smaller bricks");
+}
+
+__global__ void bin_kernel(const VolDesc *vols, int n_vols, int64_t total, int3 B, uint32_t *keys, uint32_t *vals)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        int v = 0;
+        for (int i = 1; i < n_vols; ++i)
+            if (vols[i].contour_base <= g) v = i;
+        const VolDesc &V = vols[v];
+        const int64_t k = g - V.contour_base;
+        const int Bd[3] = {B.x, B.y, B.z};
+        int bi[3];
+        for (int d = 0; d < 3; ++d) {
+            const float c = V.state[d * V.C + k];
+            int idx = (int)floorf(c * V.inv_sp[d]);
+            idx = idx < 0 ? 0 : (idx >= V.n[d] ? V.n[d] - 1 : idx);
+            int b = idx / Bd[d];
+            bi[d] = b >= V.nb[d] ? V.nb[d] - 1 : b;
+        }
+        keys[g] = (uint32_t)(V.brick_base + bi[0] + (int64_t)V.nb[0] * (bi[1] + (int64_t)V.nb[1] * bi[2]));
+        vals[g] = (uint32_t)g;
+    }
+}
+
+CUtensorMapDataType tma_type(ac_dtype t)
+{
+    switch (t) {
+    case AC_U8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    case AC_U16: return CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    case AC_F16: return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    default: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    }
+}
+
+VolDesc make_desc(const ac_contours *c, uint64_t seed)
+{
+    const ac_volume *v = c->vol;
+    VolDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.data = v->data;
+    d.pitch_y = v->pitch_y;
+    d.pitch_z = v->pitch_z;
+    for (int i = 0; i < 3; ++i) {
+        d.n[i] = (int32_t)v->n[i];
+        d.sp[i] = v->sp[i];
+        d.inv_sp[i] = 1.0f / v->sp[i];
+        d.box_hi[i] = (float)((double)(v->n[i] - 1) * v->sp[i]);
+    }
+    d.scale = v->scale;
+    d.state = c->state;
+    d.C = c->C;
+    d.key0 = (uint32_t)seed;
+    d.key1 = (uint32_t)(seed >> 32);
+    return d;
+}
+
+cudaError_t launch_evolve(ac_dtype t, const EvolveArgs &a, const Plan &pl, int64_t grid, cudaStream_t st)
+{
+    switch (t) {
+    case AC_U8: return launch_evolve_u8(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
+    case AC_U16: return launch_evolve_u16(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
+    case AC_F16: return launch_evolve_f16(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
+    default: return launch_evolve_f32(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
+    }
+}
+
+// Shared by ac_evolve and ac_evolve_batch.  sets[0] owns the scratch buffers.
+ac_status evolve_sets(ac_contours *const *sets, const uint64_t *seeds, int n_sets, const ac_evolve_params *p,
+                      const ac_trace *trace, cudaStream_t st)
+{
+    ac_status s = check_params(p);
+    if (s != AC_OK) return s;
+    const ac_volume *v0 = sets[0]->vol;
+    double stride_hint = 0, r_hint = 0;
+    int64_t total = 0;
+    for (int i = 0; i < n_sets; ++i) {
+        if (!sets[i] || !sets[i]->vol) AC_FAIL(AC_ERR_ARG, "ac_evolve: NULL contour set");
+        if (sets[i]->vol->dtype != v0->dtype || sets[i]->vol->ndim != v0->ndim)
+            AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: every set must share dtype and ndim");
+        stride_hint = std::max(stride_hint, sets[i]->stride_hint);
+        r_hint = std::max(r_hint, sets[i]->r_hint);
+        total += sets[i]->C;
+    }
+    if (total >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve: too many contours in one launch");
+    Plan pl;
+    s = plan_evolve(v0, stride_hint, r_hint, p, pl);
+    if (s != AC_OK) return s;
+
+    EvolveArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_vols = n_sets;
+    a.ndim = v0->ndim;
+    a.total_contours = total;
+    a.N = p->N;
+    a.T = p->T;
+    a.stream_id = p->stream_id;
+    a.first_iter = p->first_iter ? p->first_iter : 1;
+    a.last_iter = a.first_iter + p->T - 1;
+    a.update_last = p->update_last ? 1 : 0;
+    a.eps0 = p->eps0;
+    a.dR = p->dR;
+    a.Rmin = p->Rmin;
+    a.Rmax = p->Rmax;
+    a.max_step = p->max_step;
+    a.status = sets[0]->status;
+    if (trace && trace->device_buf) {
+        if (n_sets != 1) AC_FAIL(AC_ERR_ARG, "ac_evolve: trace is supported for a single set");
+        if (trace->k_begin < 0 || trace->k_end > sets[0]->C || trace->k_begin > trace->k_end || trace->t_begin < 1 ||
+            trace->t_begin < a.first_iter || trace->t_end > a.last_iter + 1 || trace->t_begin > trace->t_end)
+            AC_FAIL(AC_ERR_ARG, "ac_evolve: trace range outside the contours or iterations");
+        a.trace = trace->device_buf;
+        a.tk0 = trace->k_begin;
+        a.tk1 = trace->k_end;
+        a.tt0 = trace->t_begin;
+        a.tt1 = trace->t_end;
+    }
+    if (total == 0) return AC_OK;
+
+    Scratch &sc = sets[0]->scratch;
+    std::vector<VolDesc> desc(n_sets);
+    int64_t bricks = 0, cbase = 0;
+    for (int i = 0; i < n_sets; ++i) {
+        desc[i] = make_desc(sets[i], seeds ? seeds[i] : p->seed);
+        desc[i].contour_base = cbase;
+        cbase += sets[i]->C;
+        if (pl.brick) {
+            int64_t nb = 1;
+            for (int d = 0; d < 3; ++d) {
+                desc[i].nb[d] = (int32_t)((sets[i]->vol->n[d] + pl.B[d] - 1) / pl.B[d]);
+                nb *= desc[i].nb[d];
+            }
+            desc[i].brick_base = bricks;
+            bricks += nb;
+        }
+    }
+    if (bricks >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve: too many bricks");
+    AC_CUDA(sc.desc.ensure(sizeof(VolDesc) * n_sets));
+    AC_CUDA(cudaMemcpyAsync(sc.desc.p, desc.data(), sizeof(VolDesc) * n_sets, cudaMemcpyHostToDevice, st));
+    a.vols = sc.desc.as<VolDesc>();
+
+    ac_contours *owner = sets[0];
+    if (!owner->ev0) {
+        AC_CUDA(cudaEventCreate(&owner->ev0));
+        AC_CUDA(cudaEventCreate(&owner->ev1));
+    }
+    if (!pl.brick) {
+        const int64_t per_cta = (int64_t)pl.warps * 32 / pl.G;
+        const int64_t grid = std::min<int64_t>((total + per_cta - 1) / per_cta, (int64_t)1 << 30);
+        AC_CUDA(cudaEventRecord(owner->ev0, st));
+        for (int n = a.first_iter; n <= a.last_iter; ++n) {
+            a.iter0 = n;
+            cudaError_t e = launch_evolve(v0->dtype, a, pl, grid, st);
+            if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: plain launch: ") + cudaGetErrorString(e));
+            count_launch();
+        }
+        AC_CUDA(cudaEventRecord(owner->ev1, st));
+        owner->timed = true;
+        return AC_OK;
+    }
+
+    // tensor maps: one box of the staged-region size per volume
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) AC_FAIL(AC_ERR_CUDA, "ac_evolve: cuTensorMapEncodeTiled is not available from the driver");
+    std::vector<CUtensorMap> maps(n_sets);
+    for (int i = 0; i < n_sets; ++i) {
+        const ac_volume *v = sets[i]->vol;
+        cuuint64_t gdim[3] = {(cuuint64_t)v->n[0], (cuuint64_t)v->n[1], (cuuint64_t)v->n[2]};
+        cuuint64_t gstride[2] = {(cuuint64_t)(v->pitch_y * v->es), (cuuint64_t)(v->pitch_z * v->es)};
+        cuuint32_t box[3] = {(cuuint32_t)pl.ext[0], (cuuint32_t)pl.ext[1], (cuuint32_t)pl.ext[2]};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&maps[i], tma_type(v->dtype), 3, v->data, gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) AC_FAIL(AC_ERR_CUDA, "ac_evolve: cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+    }
+    AC_CUDA(sc.tmaps.ensure(sizeof(CUtensorMap) * n_sets + 128));
+    CUtensorMap *dmaps = reinterpret_cast<CUtensorMap *>(((uintptr_t)sc.tmaps.p + 127) & ~(uintptr_t)127);
+    AC_CUDA(cudaMemcpyAsync(dmaps, maps.data(), sizeof(CUtensorMap) * n_sets, cudaMemcpyHostToDevice, st));
+
+    // bin contours by brick (their current centre) and sort by brick
+    AC_CUDA(sc.keys.ensure(sizeof(uint32_t) * total));
+    AC_CUDA(sc.vals.ensure(sizeof(uint32_t) * total));
+    AC_CUDA(sc.skeys.ensure(sizeof(uint32_t) * total));
+    AC_CUDA(sc.svals.ensure(sizeof(uint32_t) * total));
+    {
+        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 1 << 16);
+        bin_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.vols, n_sets, total, make_int3(pl.B[0], pl.B[1], pl.B[2]),
+                                                     sc.keys.as<uint32_t>(), sc.vals.as<uint32_t>());
+        count_launch();
+        AC_CUDA(cudaGetLastError());
+    }
+    int end_bit = 1;
+    while (((int64_t)1 << end_bit) < bricks + 1) ++end_bit;
+    size_t tmp = 0;
+    AC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, sc.keys.as<uint32_t>(), sc.skeys.as<uint32_t>(),
+                                            sc.vals.as<uint32_t>(), sc.svals.as<uint32_t>(), (int)total, 0, end_bit, st));
+    AC_CUDA(sc.cub.ensure(tmp));
+    AC_CUDA(cub::DeviceRadixSort::SortPairs(sc.cub.p, tmp, sc.keys.as<uint32_t>(), sc.skeys.as<uint32_t>(),
+                                            sc.vals.as<uint32_t>(), sc.svals.as<uint32_t>(), (int)total, 0, end_bit, st));
+
+    a.tmaps = dmaps;
+    a.sorted_brick = sc.skeys.as<uint32_t>();
+    a.sorted_gidx = sc.svals.as<uint32_t>();
+    a.total_bricks = bricks;
+    for (int d = 0; d < 3; ++d) {
+        a.B[d] = pl.B[d];
+        a.halo[d] = pl.halo[d];
+        a.ext[d] = pl.ext[d];
+    }
+    a.smem_bytes = pl.smem;
+    AC_CUDA(cudaEventRecord(owner->ev0, st));
+    cudaError_t e = launch_evolve(v0->dtype, a, pl, bricks, st);
+    if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: brick launch: ") + cudaGetErrorString(e));
+    count_launch();
+    AC_CUDA(cudaEventRecord(owner->ev1, st));
+    owner->timed = true;
+    return AC_OK;
+}
+
+}  // namespace
+
+extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_trace *trace,
+                               void *cuda_stream)
+{
+    g_err.clear();
+    if (!ctr) AC_FAIL(AC_ERR_ARG, "ac_evolve: ctr is NULL");
+    return evolve_sets(&ctr, nullptr, 1, params, trace, (cudaStream_t)cuda_stream);
+}
+
+extern "C" ac_status ac_evolve_batch(ac_contours *const *sets, const uint64_t *seeds, int32_t n_sets,
+                                     const ac_evolve_params *params, void *cuda_stream)
+{
+    g_err.clear();
+    if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: need 1..4096 sets");
+    return evolve_sets(sets, seeds, n_sets, params, nullptr, (cudaStream_t)cuda_stream);
+}
+
+extern "C" ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms)
+{
+    g_err.clear();
+    if (!ctr || !ms) AC_FAIL(AC_ERR_ARG, "ac_evolve_kernel_ms: NULL argument");
+    if (!ctr->timed) AC_FAIL(AC_ERR_STATE, "ac_evolve_kernel_ms: no evolution recorded on this handle");
+    AC_CUDA(cudaEventSynchronize(ctr->ev1));
+    AC_CUDA(cudaEventElapsedTime(ms, ctr->ev0, ctr->ev1));
+    return AC_OK;
+}
+
+extern "C" ac_status ac_localize(ac_contours *ctr, const ac_localize_params *params, ac_cell *out_host, int64_t cap,
+                                 int64_t *n_out, void *cuda_stream)
+{
+    g_err.clear();
+    if (!ctr || !params || !n_out || cap < 0 || (cap > 0 && !out_host)) AC_FAIL(AC_ERR_ARG, "ac_localize: bad arguments");
+    if (std::isnan(params->E0)) AC_FAIL(AC_ERR_ARG, "ac_localize: E0 is NaN");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    ac_status s = check_status(ctr, st);
+    if (s != AC_OK) return s;
+    return localize_impl(ctr, params->E0, out_host, cap, n_out, st);
+}

@@ -1,0 +1,11 @@
+// Instantiations of the evolution kernels for float voxels (see ac_evolve.cuh).
+#include "ac_evolve.cuh"
+#include "ac_host.h"
+
+namespace ac {
+cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+                             cudaStream_t st)
+{
+    return launch_evolve_t<float>(a, brick, G, comp, warps, grid, st);
+}
+}  // namespace ac

@@ -1,0 +1,96 @@
+// ac_host.h -- host-side internals of libac shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ac_internal.cuh"
+
+struct ac_volume {
+    int device;
+    ac_dtype dtype;
+    int ndim;
+    int64_t n[3];
+    float sp[3];
+    float scale;
+    int es;               // bytes per voxel
+    void *data;           // row-pitched copy
+    int64_t pitch_y;      // elements per row
+    int64_t pitch_z;      // elements per plane
+    size_t bytes;
+};
+
+namespace ac {
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes + bytes / 4 + 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct Scratch {
+    DevBuf keys, vals, skeys, svals, cub, desc, tmaps;               // evolve
+    DevBuf flags, surv, ekeys, surv_sorted, pos, cellk, celli, cellk_s, celli_s, cell_start, stat, acc,
+        cells, counters;                                               // localize
+    void release_all();
+};
+
+}  // namespace ac
+
+struct ac_contours {
+    ac_volume *vol;
+    int64_t C;
+    float *state;         // 5 x C
+    int32_t *status;      // device status word
+    double stride_hint;   // lattice stride (or mean spacing of explicit seeds)
+    double r_hint;        // largest initial radius
+    ac::Scratch scratch;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last evolution kernel(s)
+    bool lattice = false;                       // lattice-seeded: parameters below
+    int64_t L[3] = {1, 1, 1};
+    float first[3] = {0, 0, 0};
+    float stride = 0, R0 = 0;
+    bool timed = false;
+};
+
+namespace ac {
+
+// thread-local error message
+void set_error(const std::string &msg);
+// count of the library's own kernel launches
+void count_launch(int64_t n = 1);
+
+cudaError_t launch_evolve_u8(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+                             cudaStream_t st);
+cudaError_t launch_evolve_u16(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+                              cudaStream_t st);
+cudaError_t launch_evolve_f16(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+                              cudaStream_t st);
+cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+                              cudaStream_t st);
+
+// localization (ac_localize.cu); returns an ac_status and sets the message
+ac_status localize_impl(ac_contours *ctr, float E0, ac_cell *out_host, int64_t cap, int64_t *n_out,
+                        cudaStream_t st);
+
+}  // namespace ac

@@ -1,0 +1,329 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Per-iteration (teacher-forced) energies and gradients within 1e-5 of the oracle's
+magnitude-scaled value, final centres within 0.25 voxel, detection-set agreement
+>= 0.999, identical Philox words and identical localization on identical inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ac():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_06304_gb300 import ac as lib
+    lib.load()
+    return lib
+
+
+@pytest.fixture(scope="module")
+def small3d():
+    from paper_1804_06304_gb300 import synth
+    return synth.small_3d(0)
+
+
+def _p3(ac, s, **kw):
+    R0 = 4.0 / math.sqrt(1.5)
+    base = dict(N=256, T=50, seed=1234)
+    base.update(kw)
+    return ac.default_params(3, R0, s.contrast, **base)
+
+
+# ------------------------------------------------------------------ random numbers
+def test_philox_bits_match_oracle(ac, oracle):
+    import torch
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(1_000_000, 4), dtype=np.uint64).astype(np.uint32)
+    key = 0x0123456789ABCDEF
+    got = ac.ac_philox4x32_10(torch.from_numpy(ctr.view(np.int32)).cuda(), key).cpu().numpy().view(np.uint32)
+    want = oracle.philox(ctr, [key & 0xFFFFFFFF, key >> 32])
+    np.testing.assert_array_equal(got, want)
+
+
+# ------------------------------------------------------------------ seeding
+@pytest.mark.parametrize("ndim,shape,sp,stride", [(3, (64, 64, 32), (1, 1, 1), 4.0), (2, (512, 300), (1, 1), 6.0),
+                                                  (3, (96, 96, 48), (1, 1, 2), 6.0)])
+def test_lattice_matches_oracle(ac, oracle, ndim, shape, sp, stride):
+    vol = np.zeros(shape[::-1], np.uint8)
+    V = ac.ac_create_volume(vol, sp)
+    C = ac.ac_seed(V, stride=stride)
+    st = ac.ac_get_state(C)
+    want = oracle.seed_lattice(ndim, shape, sp, stride)
+    assert st.shape[1] == len(want)
+    np.testing.assert_allclose(st[:4].T, want, rtol=2e-7, atol=1e-6)
+    assert np.all(st[4] == 0)
+
+
+# ------------------------------------------------------------------ teacher-forced 3D
+@pytest.mark.parametrize("path,G,comp", [(0, 32, 1), (0, 16, 1), (0, 8, 1), (0, 32, 0), (1, 32, 1), (1, 16, 0)])
+def test_teacher_forced_small3d(ac, oracle, small3d, path, G, comp):
+    s = small3d
+    p = _p3(ac, s, path=path, lanes_per_contour=G, compensated=comp)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0, trace_k=(0, 2048))
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], 0, 1)
+    assert frac >= 0.9999, (frac, nflag, worst, bad)
+    assert nflag < 0.01 * r["trace"].shape[0] * r["trace"].shape[1]
+    # the trace's first state is the seed, its last E is the reported energy
+    np.testing.assert_array_equal(r["trace"][0, :, :4].T, r["init"][:4])
+    np.testing.assert_array_equal(r["trace"][-1, :, 4], r["final"][4])
+    np.testing.assert_array_equal(r["trace"][-1, :, :4].T, r["final"][:4])
+
+
+def test_update_rule_matches_oracle(ac, oracle, small3d):
+    """State n+1 = oracle update (Eqs. 12-15 + clamps) of state n with the GPU's own
+    evaluation results."""
+    s = small3d
+    p = _p3(ac, s, T=12)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0, trace_k=(0, 2048))
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    op = P.oracle_params(oracle, 3, p)
+    tr = r["trace"].astype(np.float64)
+    rng = np.random.default_rng(1)
+    for n in range(1, 12):
+        for k in rng.choice(2048, 60, replace=False):
+            cx, cy, cz, R, E, dEdR, gx, gy, gz = tr[n - 1, k]
+            res = np.zeros(oracle.RES_LEN)
+            # (c, R) gradients to the identifier-point partials: dE/dp = (dE/dc - dE/dR e_x)/2, dE/dq = (dE/dc + dE/dR e_x)/2
+            res[oracle.DEDP:oracle.DEDP + 3] = [(gx - dEdR) / 2, gy / 2, gz / 2]
+            res[oracle.DEDQ:oracle.DEDQ + 3] = [(gx + dEdR) / 2, gy / 2, gz / 2]
+            pq, qq = oracle.update_pq(img, op, n, res, [cx - R, cy, cz], [cx + R, cy, cz])
+            want = np.array([(pq[0] + qq[0]) / 2, pq[1], pq[2], (qq[0] - pq[0]) / 2])
+            np.testing.assert_allclose(tr[n, k, :4], want, atol=2e-5, rtol=2e-6)
+
+
+# ------------------------------------------------------------------ free running + localize
+def test_free_running_and_detections_small3d(ac, oracle, small3d):
+    s = small3d
+    p = _p3(ac, s)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0)
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    op = P.oracle_params(oracle, 3, p)
+    cR0 = r["init"][:4].T.astype(np.float64)
+    cR, E, _ = oracle.evolve(img, op, cR0)
+    gpu = r["final"]
+    d = np.linalg.norm(gpu[:3].T - cR[:, :3], axis=1)
+    assert np.mean(d <= 0.25) >= 0.99, np.mean(d <= 0.25)
+    E0 = ac.default_E0(3, s.contrast)
+    cells = ac.ac_localize(r["ctr"], E0)
+    ids_o = oracle.localize(3, cR, E, E0)
+    m = P.match_sets(np.stack([c for c in cells["c"]]) if len(cells) else np.zeros((0, 3)), cR[ids_o, :3], 0.5)
+    agree = 2 * m / (len(cells) + len(ids_o))
+    assert agree >= 0.999, (agree, len(cells), len(ids_o))
+    assert len(cells) >= 18
+
+
+def test_localize_identical_on_identical_state(ac, oracle, small3d):
+    s = small3d
+    p = _p3(ac, s, T=30)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0)
+    st = r["final"].astype(np.float64)
+    for E0 in (ac.default_E0(3, s.contrast), -5.0, 0.0, 1e9):
+        cells = ac.ac_localize(r["ctr"], E0)
+        want = oracle.localize(3, st[:4].T, st[4], float(np.float32(E0)))
+        assert list(cells["id"]) == list(want)
+        if len(want):
+            np.testing.assert_array_equal(cells["E"], r["final"][4][want])
+            np.testing.assert_allclose(cells["r"], r["final"][3][want] * 2 ** (-1 / 3), rtol=1e-6)
+    assert len(ac.ac_localize(r["ctr"], -1e9)) == 0
+    part = ac.ac_localize(r["ctr"], 1e9, cap=3)
+    assert len(part) == 3
+
+
+def test_localize_hand_built_cases(ac, oracle):
+    vol = np.zeros((8, 40, 40), np.uint8)
+    V = ac.ac_create_volume(vol)
+    rho = 2 ** (-1 / 3)
+    seeds = np.array([[10, 10, 3, 5.0], [13.5, 10, 3, 5.0], [17, 10, 3, 5.0],     # chain
+                      [10, 30, 3, 4.0], [11, 30, 3, 4.0],                           # tie
+                      [30, 30, 3, 2.0], [30, 20, 3, 2.0]], np.float32)              # threshold
+    C = ac.ac_seed(V, explicit=seeds)
+    st = ac.ac_get_state(C)
+    st[4] = [-10, -9, -8, -4, -4, -3, -2.5]
+    ac.ac_set_state(C, st)
+    cells = ac.ac_localize(C, -3.0)
+    assert list(cells["id"]) == [0, 3, 2, 5] == list(oracle.localize(3, st[:4].T.astype(float), st[4].astype(float), -3.0))
+
+
+# ------------------------------------------------------------------ 2D
+@pytest.fixture(scope="module")
+def crop2d():
+    from paper_1804_06304_gb300 import synth
+    return synth.large_2d(1, shape=(512, 512), n_nuclei=188)
+
+
+@pytest.mark.parametrize("path,G", [(0, 32), (0, 16), (1, 32)])
+def test_teacher_forced_2d(ac, oracle, crop2d, path, G):
+    s = crop2d
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=99, path=path, lanes_per_contour=G)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(1000, 2500))
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 1000, 1)
+    assert frac >= 0.9999, (frac, nflag, worst, bad)
+
+
+def test_free_running_and_detections_2d(ac, oracle, crop2d):
+    s = crop2d
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=99)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0)
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    cR, E, _ = oracle.evolve(img, P.oracle_params(oracle, 2, p), r["init"][:4].T.astype(np.float64))
+    d = np.linalg.norm(r["final"][:2].T - cR[:, :2], axis=1)
+    assert np.mean(d <= 0.25) >= 0.99, np.mean(d <= 0.25)
+    E0 = ac.default_E0(2, s.contrast)
+    cells = ac.ac_localize(r["ctr"], E0)
+    ids_o = oracle.localize(2, cR, E, E0)
+    m = P.match_sets(np.stack(cells["c"])[:, :2], cR[ids_o, :2], 0.5)
+    agree = 2 * m / (len(cells) + len(ids_o))
+    assert agree >= 0.99, (agree, len(cells), len(ids_o))
+
+
+# ------------------------------------------------------------------ storage types, anisotropy
+@pytest.fixture(scope="module")
+def brain_small():
+    from paper_1804_06304_gb300 import synth
+    return synth.brain_3d(2, shape=(96, 96, 48), n_nuclei=170)
+
+
+@pytest.mark.parametrize("kind", ["u16", "f16", "f32"])
+def test_teacher_forced_storage_types(ac, oracle, brain_small, kind):
+    s = brain_small
+    vol = {"u16": s.volume, "f16": s.volume_f16, "f32": s.volume.astype(np.float32)}[kind]
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(3, R0, s.contrast, N=512, T=10, seed=5)
+    r = P.gpu_run(ac, vol, s.spacing, p, stride=6.0, trace_k=(0, 4096), scale=0.5, device_volume=(kind == "f32"))
+    img = P.oracle_image(oracle, vol, s.spacing, scale=0.5)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], 0, 1)
+    assert frac >= 0.9999, (frac, nflag, worst, bad)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("N,T,G", [(1, 3, 32), (33, 4, 32), (100, 5, 16), (7, 2, 8)])
+def test_ragged_sample_counts(ac, oracle, small3d, N, T, G):
+    s = small3d
+    p = _p3(ac, s, N=N, T=T, lanes_per_contour=G)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0, trace_k=(100, 700))
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], 100, 1)
+    assert frac >= 0.9999, (frac, worst, bad)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_tiny_volumes_and_out_of_volume_balls(ac, oracle, ndim):
+    rng = np.random.default_rng(3)
+    shape = (3, 2, 2)[:ndim] if ndim == 3 else (2, 5)
+    vol = rng.integers(0, 255, size=shape[::-1], dtype=np.uint8)
+    seeds = np.array([[0.0, 0.0, 0.0, 3.0], [1.7, 0.9, 0.4, 6.0], [2.0, 1.0, 1.0, 1.0], [0.5, 0.5, 0.5, 0.7]],
+                     np.float32)
+    if ndim == 2:
+        seeds[:, 2] = 0
+        seeds[:, 0] = np.minimum(seeds[:, 0], 1.0)
+    for path in (0, 1):
+        p = ac.EvolveParams(N=64, T=6, eps0=0.3, dR=1.0, Rmin=0.5, Rmax=9.0, seed=8, path=path)
+        r = P.gpu_run(ac, vol, (1, 1, 1), p, explicit=seeds, trace_k=(0, 4))
+        img = P.oracle_image(oracle, vol, (1, 1, 1))
+        frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, ndim, p), r["trace"], 0, 1)
+        assert frac == 1.0, (path, worst, bad)
+
+
+def test_global_fallback_when_contours_outgrow_the_halo(ac, oracle):
+    """Seeds with a tiny radius give a small halo; on a big blob they grow out of
+    the staged region and read the global volume -- same results either way."""
+    from paper_1804_06304_gb300 import synth
+    vol = synth.sphere_volume((48, 48, 48), (23.7, 24.2, 23.9), 9.0)
+    seeds = np.array([[23 + dx, 24 + dy, 24, 1.0] for dx in (-2, 0, 2) for dy in (-2, 0, 2)], np.float32)
+    p = ac.EvolveParams(N=256, T=30, eps0=8.0 / 170.0, dR=1.0, Rmin=0.5, Rmax=20.0, seed=3)
+    r = P.gpu_run(ac, vol, (1, 1, 1), p, explicit=seeds, trace_k=(0, 9))
+    assert r["final"][3].max() > 6.0          # grew well past the halo of ~5 voxels
+    img = P.oracle_image(oracle, vol, (1, 1, 1))
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], 0, 1)
+    assert frac == 1.0, (worst, bad)
+    p2 = ac.EvolveParams(**{**p.__dict__, "path": 1})
+    r2 = P.gpu_run(ac, vol, (1, 1, 1), p2, explicit=seeds)
+    np.testing.assert_array_equal(r["final"], r2["final"])
+
+
+def test_brick_and_plain_paths_agree_bitwise(ac, small3d):
+    s = small3d
+    a = P.gpu_run(ac, s.volume, s.spacing, _p3(ac, s, T=20), stride=4.0)
+    b = P.gpu_run(ac, s.volume, s.spacing, _p3(ac, s, T=20, path=1), stride=4.0)
+    np.testing.assert_array_equal(a["final"], b["final"])
+
+
+def test_resume_equals_uninterrupted(ac, small3d):
+    s = small3d
+    full = P.gpu_run(ac, s.volume, s.spacing, _p3(ac, s, T=30), stride=4.0)
+    V = ac.ac_create_volume(s.volume)
+    C = ac.ac_seed(V, stride=4.0)
+    ac.ac_evolve(C, _p3(ac, s, T=12, update_last=1))
+    saved = ac.ac_get_state(C)
+    C2 = ac.ac_seed(V, stride=4.0)
+    ac.ac_set_state(C2, saved)
+    ac.ac_evolve(C2, _p3(ac, s, T=18, first_iter=13))
+    np.testing.assert_array_equal(ac.ac_get_state(C2), full["final"])
+
+
+def test_batch_equals_single(ac):
+    from paper_1804_06304_gb300 import synth
+    vols = synth.batch_3d(3, count=4, max_scale=0.3)
+    p = ac.default_params(3, 4.0 / math.sqrt(1.5), 170.0, N=128, T=15)
+    singles, sets, keep = [], [], []
+    for i, s in enumerate(vols):
+        r = P.gpu_run(ac, s.volume, s.spacing, ac.EvolveParams(**{**p.__dict__, "seed": 100 + i}), stride=4.0)
+        singles.append(r["final"])
+        V = ac.ac_create_volume(s.volume)
+        keep.append(V)
+        sets.append(ac.ac_seed(V, stride=4.0))
+    ac.ac_evolve_batch(sets, p, seeds=[100 + i for i in range(len(vols))])
+    for c, want in zip(sets, singles):
+        np.testing.assert_array_equal(ac.ac_get_state(c), want)
+
+
+def test_nonfinite_volume_is_reported(ac):
+    vol = np.full((16, 16, 16), 5.0, np.float32)
+    vol[8, 8, 8] = np.nan
+    V = ac.ac_create_volume(vol)
+    C = ac.ac_seed(V, stride=4.0)
+    ac.ac_evolve(C, ac.EvolveParams(N=64, T=3, eps0=0.1, Rmin=0.5, Rmax=9.0))
+    with pytest.raises(ac.ACError) as e:
+        ac.ac_get_state(C)
+    assert e.value.status == ac.AC_ERR_NUMERIC
+
+
+def test_invalid_parameters_rejected(ac, small3d):
+    V = ac.ac_create_volume(small3d.volume)
+    C = ac.ac_seed(V, stride=4.0)
+    bad = [dict(N=0), dict(T=0), dict(dR=0.0), dict(Rmin=2.0, Rmax=1.0), dict(max_step=0.0),
+           dict(lanes_per_contour=4), dict(path=7), dict(eps0=float("nan")), dict(brick=(300, 8, 8))]
+    for b in bad:
+        p = _p3(ac, small3d, T=2)
+        p = ac.EvolveParams(**{**p.__dict__, **b})
+        with pytest.raises(ac.ACError) as e:
+            ac.ac_evolve(C, p)
+        assert e.value.status == ac.AC_ERR_ARG, b
+
+
+# ------------------------------------------------------------------ full size, sampled
+def test_full_size_2d_sampled_parity(ac, oracle):
+    """The 4096^2 workload in the benchmark's launch configuration; the oracle
+    re-evaluates a sampled stripe of contours at every iteration."""
+    from paper_1804_06304_gb300 import synth
+    s = synth.large_2d(1)
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=7)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(200_000, 200_256))
+    assert r["final"].shape[1] == 682 * 682
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 200_000, 1)
+    assert frac >= 0.9999, (frac, worst, bad)
+    assert np.all(np.isfinite(r["final"]))
