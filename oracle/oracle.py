@@ -230,8 +230,8 @@ def energy_grid(img, ndim, c, R, dR) -> float:
 
 
 def update_pq(img, params, it, res, p, q):
-    p = np.array(p, dtype=np.float64)
-    q = np.array(q, dtype=np.float64)
+    p = np.array(p, dtype=np.float64, order="C")
+    q = np.array(q, dtype=np.float64, order="C")
     res = np.ascontiguousarray(res, dtype=np.float64)
     lib().or_update_pq(ct.byref(img.s), ct.byref(params), it, _P(res, ct.c_double), _P(p, ct.c_double),
                        _P(q, ct.c_double))
@@ -240,7 +240,7 @@ def update_pq(img, params, it, res, p, q):
 
 def evolve(img, params, cR: np.ndarray, ids=None, trace: bool = False, nthreads: int = 0):
     """Returns (final cR (C x 4), E (C,), trace (T x C x 9) or None)."""
-    cR = np.array(cR, dtype=np.float64).reshape(-1, 4)
+    cR = np.array(cR, dtype=np.float64, order="C").reshape(-1, 4)   # a C-ordered copy (updated in place)
     C = len(cR)
     ids = np.arange(C, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
     E = np.empty(C)

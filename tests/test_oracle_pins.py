@@ -468,6 +468,20 @@ def test_convergence_noise_free_blob(oracle, ndim):
     assert E[0] < 0
 
 
+def test_wrapper_accepts_non_contiguous_state(oracle):
+    """Marshalling: a transposed (Fortran-ordered) state array evolves like its
+    C-ordered copy."""
+    from paper_1804_06304_gb300 import synth
+    vol = synth.sphere_volume((24, 24, 24), (11.5, 12.2, 11.9), 5.0)
+    img = oracle.VolumeImage(vol)
+    P = oracle.make_params(3, 64, 4, eps0=0.3, Rmin=1.0, Rmax=9.0, seed=2)
+    soa = np.array([[10.0, 13.0, 11.0], [12.0, 11.0, 12.5], [11.0, 12.0, 12.0], [4.0, 3.5, 3.0]], np.float32)
+    a = oracle.evolve(img, P, soa.T.astype(np.float64))[0]
+    b = oracle.evolve(img, P, np.ascontiguousarray(soa.T, dtype=np.float64))[0]
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_allclose(a[:, :3], b[:, :3])
+
+
 # ----------------------------------------------------------------------------- lattice, localize
 def test_lattice_spacing_and_count(oracle):
     """Fig. 1b / Fig. 4b: neighbours sqrt(1.5) R0 apart; stride 4 over 64x64x32 gives 16x16x8."""
