@@ -58,12 +58,15 @@ WORKLOADS = {
 }
 
 
-def make_input(name: str, seed: int, dtype: str):
+def make_input(name: str, seed: int, dtype: str, size: int = 0):
     from paper_1804_06304_gb300 import synth
     if name == "large-2d":
-        s = synth.large_2d(seed)
+        side = size or 4096
+        s = synth.large_2d(seed, shape=(side, side), n_nuclei=int(round(12_000 * side * side / 4096**2)))
     elif name == "brain-3d":
-        s = synth.brain_3d(seed, with_f16=(dtype == "f16"))
+        side = size or 1024
+        s = synth.brain_3d(seed, shape=(side, side, side // 4), n_nuclei=int(round(100_000 * (side / 1024) ** 3)),
+                           with_f16=(dtype == "f16"))
     else:
         s = synth.small_3d(seed)
     vol = s.volume_f16 if dtype == "f16" else s.volume
@@ -172,6 +175,7 @@ def main(argv=None):
     ap.add_argument("--compensated", type=int, default=1)
     ap.add_argument("--brick", type=str, default="0,0,0")
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--size", type=int, default=0, help="image side (smaller instances for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -197,7 +201,7 @@ def main(argv=None):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    s, vol = make_input(args.workload, wl["seed"] + rank, args.dtype)
+    s, vol = make_input(args.workload, wl["seed"] + rank, args.dtype, args.size)
     spacing = s.spacing
     ndim = wl["ndim"]
     C_expected = lattice_count(s.shape_xyz, spacing, wl["stride"], ndim)
@@ -304,7 +308,8 @@ def main(argv=None):
             "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 arithmetic on " + str(vol.dtype) + " voxels", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "contours": C.count, "samples": wl["N"],
+            "config": {"workload": args.workload + (f"@{args.size}" if args.size else ""), "desc": wl["desc"],
+                       "contours": C.count, "samples": wl["N"],
                        "iterations": wl["T"], "path": args.path, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "voxels_per_s": world * int(np.prod(vol.shape)) / (t_ms * 1e-3),
@@ -323,7 +328,7 @@ def reference_arm(args, wl, rank, world):
     the same workload's contours (all iterations)."""
     if rank != 0:
         return
-    s, vol = make_input(args.workload, wl["seed"], args.dtype)
+    s, vol = make_input(args.workload, wl["seed"], args.dtype, args.size)
     per_step = max(2.0, min(15.0, 120.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup):
         oracle_sample(s, vol, wl, s.spacing, per_step, rng_seed=100 + i)
