@@ -150,7 +150,8 @@ def test_localize_hand_built_cases(ac, oracle):
     st[4] = [-10, -9, -8, -4, -4, -3, -2.5]
     ac.ac_set_state(C, st)
     cells = ac.ac_localize(C, -3.0)
-    assert list(cells["id"]) == [0, 3, 2, 5] == list(oracle.localize(3, st[:4].T.astype(float), st[4].astype(float), -3.0))
+    # acceptance follows increasing (E, k): 0 kept, 1 overlaps 0, 2 kept, 3 kept, 4 overlaps 3 (tie, higher k), 5 kept
+    assert list(cells["id"]) == [0, 2, 3, 5] == list(oracle.localize(3, st[:4].T.astype(float), st[4].astype(float), -3.0))
 
 
 # ------------------------------------------------------------------ 2D
