@@ -153,6 +153,10 @@ typedef struct {
     int32_t update_last;       /* 1: also update after the last evaluation (a run
                                   continued by a later call with first_iter =
                                   first_iter + T then equals one uninterrupted run)   */
+    int32_t sampling;          /* sample-point arithmetic: 0 auto (accurate when N < 64),
+                                  1 accurate (correctly rounded sqrt/cbrt, ~1 ulp
+                                  sine/cosine), 2 fast (hardware approximations,
+                                  ~2^-20 absolute direction error)                    */
 } ac_evolve_params;
 
 typedef struct {
@@ -168,10 +172,12 @@ ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_t
 /*
  * ac_evolve_batch -- one launch over several contour sets, each on its own volume
  * (the batching form: uneven volumes and contour counts in one persistent pass).
- * params are shared; each set keeps its own Philox key in seeds[i] so results match
- * ac_evolve on that set alone.  Asynchronous.  Errors as ac_evolve.
+ * params are shared, including the Philox key (params->seed); set i draws its
+ * samples with the fourth counter word stream_ids[i] (NULL: params->stream_id for
+ * every set), so set i gives exactly what ac_evolve on that set alone gives with
+ * stream_id = stream_ids[i].  Asynchronous.  Errors as ac_evolve.
  */
-ac_status ac_evolve_batch(ac_contours *const *sets, const uint64_t *seeds, int32_t n_sets,
+ac_status ac_evolve_batch(ac_contours *const *sets, const uint32_t *stream_ids, int32_t n_sets,
                           const ac_evolve_params *params, void *cuda_stream);
 
 /* ------------------------------------------------------------------ localize -- */
@@ -226,6 +232,13 @@ ac_status ac_philox4x32_10(const uint32_t *ctr_dev, uint64_t key, uint32_t *out_
  * on the launching stream; binning and sorting excluded).  Synchronizes on the end
  * event.  Errors: AC_ERR_ARG, AC_ERR_STATE (nothing evolved yet), AC_ERR_CUDA. */
 ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms);
+
+/* Contour-iterations of the last ac_evolve / ac_evolve_batch on this handle by
+ * gather path: counts[0] fast (ball inside the staged region and the volume),
+ * counts[1] clamped (inside the region, crossing the volume border), counts[2]
+ * global fallback (ball outside the staged region; plain path: every one).
+ * Synchronizes the stream.  Errors: AC_ERR_ARG, AC_ERR_CUDA. */
+ac_status ac_evolve_stats(ac_contours *ctr, int64_t counts[3], void *cuda_stream);
 
 /* Number of the library's own kernel launches since it was loaded (all threads).
  * Sorting and selection steps run CUB library kernels, which are not counted. */

@@ -235,7 +235,9 @@ enum {
     OR_VAR_E = 18,    /* variance of the MC estimate of E             */
     OR_VAR_R = 19,    /* ... of dE/dR                                 */
     OR_VAR_C = 20,    /* 3: ... of dE/dc                              */
-    OR_RES_LEN = 23
+    OR_MAG_G = 23,    /* gamma V/N sum |S'(r)| I: direction-free magnitude of dE/dc */
+    OR_MAG_I = 24,    /* gamma V/N sum |I|: intensity mass of the footprint       */
+    OR_RES_LEN = 25
 };
 
 static void sample_block(const or_params *P, int64_t blk, int64_t iter, int64_t k, uint32_t w[4])
@@ -258,7 +260,7 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
     const double edges[4] = {rho * R - 0.5 * dr, rho * R + 0.5 * dr, R - 0.5 * P->dR, R + 0.5 * P->dR};
 
     double sSI = 0, sdpx = 0, sdqx = 0, sdpy = 0, sdpz = 0;
-    double mSI = 0, mdSdR = 0, mc[3] = {0, 0, 0};
+    double mSI = 0, mdSdR = 0, mc[3] = {0, 0, 0}, mg = 0, mi = 0;
     /* raw moments of the per-sample terms, for the variance of the estimates */
     double m1[5] = {0, 0, 0, 0, 0}, m2[5] = {0, 0, 0, 0, 0};
     int64_t flags = 0;
@@ -295,6 +297,8 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
         mSI += wmc * fabs(S * I);
         mdSdR += wmc * fabs(dSdR * I);
         for (int a = 0; a < d; ++a) mc[a] += wmc * fabs(dSdr * dir[a] * I);
+        mg += wmc * fabs(dSdr * I);
+        mi += wmc * fabs(I);
         {
             const double terms[5] = {S * I, (-(double)d / R * S + dSdR) * I, -dSdr * dir[0] * I,
                                      -dSdr * dir[1] * I, -dSdr * dir[2] * I};
@@ -318,6 +322,8 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
     for (int a = 0; a < 3; ++a) res[OR_MAG_C + a] = gamma * mc[a];
     res[OR_FLAGS] = (double)flags;
     res[OR_SUM_SI] = sSI;
+    res[OR_MAG_G] = gamma * mg;
+    res[OR_MAG_I] = gamma * mi;
     for (int m = 0; m < 5; ++m) {
         /* each sample's term times gamma V is an unbiased one-sample estimate */
         double mean = m1[m] / P->N, var = m2[m] / P->N - mean * mean;

@@ -22,8 +22,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-E, DEDP, DEDQ, DEDR, DEDC, MAG_E, MAG_R, MAG_C, FLAGS, SUM_SI, VAR_E, VAR_R, VAR_C, RES_LEN = (
-    0, 1, 4, 7, 8, 11, 12, 13, 16, 17, 18, 19, 20, 23)
+E, DEDP, DEDQ, DEDR, DEDC, MAG_E, MAG_R, MAG_C, FLAGS, SUM_SI, VAR_E, VAR_R, VAR_C, MAG_G, MAG_I, RES_LEN = (
+    0, 1, 4, 7, 8, 11, 12, 13, 16, 17, 18, 19, 20, 23, 24, 25)
 TRACE_LEN = 9
 DTYPES = {np.dtype(np.uint8): 0, np.dtype(np.uint16): 1, np.dtype(np.float16): 2, np.dtype(np.float32): 3}
 

@@ -39,7 +39,7 @@ class ac_evolve_params(ct.Structure):
                 ("Rmin", ct.c_float), ("Rmax", ct.c_float), ("max_step", ct.c_float), ("seed", ct.c_uint64),
                 ("stream_id", ct.c_uint32), ("path", ct.c_int32), ("lanes_per_contour", ct.c_int32),
                 ("compensated", ct.c_int32), ("brick", ct.c_int32 * 3), ("warps_per_block", ct.c_int32),
-                ("first_iter", ct.c_int32), ("update_last", ct.c_int32)]
+                ("first_iter", ct.c_int32), ("update_last", ct.c_int32), ("sampling", ct.c_int32)]
 
 
 class ac_trace(ct.Structure):
@@ -69,7 +69,7 @@ _SIGS = {
     "ac_contour_count": (ct.c_int64, [ct.c_void_p]),
     "ac_destroy_contours": (None, [ct.c_void_p]),
     "ac_evolve": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_evolve_params), ct.POINTER(ac_trace), ct.c_void_p]),
-    "ac_evolve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_uint64), ct.c_int32,
+    "ac_evolve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_uint32), ct.c_int32,
                                    ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_localize": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_localize_params), ct.c_void_p, ct.c_int64,
                                ct.POINTER(ct.c_int64), ct.c_void_p]),
@@ -79,6 +79,7 @@ _SIGS = {
     "ac_philox4x32_10": (ct.c_int, [ct.c_void_p, ct.c_uint64, ct.c_void_p, ct.c_int64, ct.c_void_p]),
     "ac_evolve_kernel_ms": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_float)]),
     "ac_kernel_launches": (ct.c_int64, []),
+    "ac_evolve_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p]),
     "ac_last_error": (ct.c_char_p, []),
 }
 
@@ -254,6 +255,7 @@ class EvolveParams:
     warps_per_block: int = 0
     first_iter: int = 0
     update_last: int = 0
+    sampling: int = 0
 
     def to_c(self) -> ac_evolve_params:
         p = ac_evolve_params()
@@ -294,13 +296,15 @@ def ac_evolve(ctr: Contours, params: EvolveParams, trace=None, stream=None):
                        ct.c_void_p(_stream(stream))))
 
 
-def ac_evolve_batch(sets, params: EvolveParams, seeds=None, stream=None):
+def ac_evolve_batch(sets, params: EvolveParams, stream_ids=None, stream=None):
+    """One launch over several contour sets; set i uses Philox counter word
+    stream_ids[i] (default params.stream_id) and the shared key params.seed."""
     l = load()
     p = params.to_c()
     arr = (ct.c_void_p * len(sets))(*[s.handle.value if isinstance(s.handle, ct.c_void_p) else s.handle for s in sets])
     sd = None
-    if seeds is not None:
-        sd = (ct.c_uint64 * len(sets))(*[int(s) for s in seeds])
+    if stream_ids is not None:
+        sd = (ct.c_uint32 * len(sets))(*[int(s) for s in stream_ids])
     _check(l.ac_evolve_batch(arr, sd, len(sets), ct.byref(p), ct.c_void_p(_stream(stream))))
 
 
@@ -347,6 +351,13 @@ def ac_evolve_kernel_ms(ctr: Contours) -> float:
     ms = ct.c_float()
     _check(load().ac_evolve_kernel_ms(ctr.handle, ct.byref(ms)))
     return float(ms.value)
+
+
+def ac_evolve_stats(ctr: Contours, stream=None) -> tuple:
+    """(fast, clamped, global) contour-iterations of the last evolution."""
+    c = (ct.c_int64 * 3)()
+    _check(load().ac_evolve_stats(ctr.handle, c, ct.c_void_p(_stream(stream))))
+    return tuple(int(v) for v in c)
 
 
 def ac_kernel_launches() -> int:

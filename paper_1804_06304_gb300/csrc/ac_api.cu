@@ -189,6 +189,8 @@ static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out)
     cudaError_t e = cudaMalloc(&c->state, sizeof(float) * 5 * (size_t)(C > 0 ? C : 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->path_counts, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->path_counts, 0, sizeof(unsigned long long) * 4);
     if (e != cudaSuccess) {
         if (c->state) cudaFree(c->state);
         delete c;
@@ -300,6 +302,7 @@ extern "C" void ac_destroy_contours(ac_contours *ctr)
     if (ctr->ev1) cudaEventDestroy(ctr->ev1);
     cudaFree(ctr->state);
     cudaFree(ctr->status);
+    cudaFree(ctr->path_counts);
     delete ctr;
 }
 
@@ -355,7 +358,7 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
-        const uint4 w = philox4x32_10(c, k0, k1);
+        const uint4 w = philox4x32_10_key(c, k0, k1);
         out[4 * i] = w.x;
         out[4 * i + 1] = w.y;
         out[4 * i + 2] = w.z;
@@ -382,9 +385,11 @@ namespace {
 
 struct Plan {
     int B[3], halo[3], ext[3];
-    int smem;
+    int raw;        // staged region bytes
+    int quad_off;   // 2D: byte offset of the float4 quads (0: none)
+    int smem;       // dynamic shared memory bytes
     int G, warps;
-    bool brick, comp;
+    bool brick, comp, acc;
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -413,12 +418,14 @@ ac_status check_params(const ac_evolve_params *p)
     if (!(p->max_step > 0.0f) || !std::isfinite(p->max_step)) AC_FAIL(AC_ERR_ARG, "ac_evolve: max_step must be positive");
     if (!(p->eps0 >= 0.0f) || !std::isfinite(p->eps0)) AC_FAIL(AC_ERR_ARG, "ac_evolve: eps0 must be >= 0");
     if (p->path != AC_PATH_BRICK && p->path != AC_PATH_PLAIN) AC_FAIL(AC_ERR_ARG, "ac_evolve: unknown path");
+    if (p->sampling < 0 || p->sampling > 2) AC_FAIL(AC_ERR_ARG, "ac_evolve: sampling must be 0, 1 or 2");
     if (p->first_iter < 0 || (int64_t)(p->first_iter ? p->first_iter : 1) + p->T > (1 << 30))
         AC_FAIL(AC_ERR_ARG, "ac_evolve: first_iter out of range");
     if (p->lanes_per_contour != 0 && p->lanes_per_contour != 8 && p->lanes_per_contour != 16 &&
         p->lanes_per_contour != 32)
         AC_FAIL(AC_ERR_ARG, "ac_evolve: lanes_per_contour must be 0, 8, 16 or 32");
-    if (p->warps_per_block < 0 || p->warps_per_block > 8) AC_FAIL(AC_ERR_ARG, "ac_evolve: warps_per_block in [0, 8]");
+    if (p->warps_per_block < 0 || p->warps_per_block > 16) AC_FAIL(AC_ERR_ARG, "ac_evolve: warps_per_block in [0, 16]");
+    if (p->path == AC_PATH_PLAIN && p->warps_per_block > 8) AC_FAIL(AC_ERR_ARG, "ac_evolve: plain path takes at most 8 warps per block");
     for (int d = 0; d < 3; ++d)
         if (p->brick[d] < 0 || p->brick[d] > 224) AC_FAIL(AC_ERR_ARG, "ac_evolve: brick sizes must be in [0, 224]");
     return AC_OK;
@@ -434,20 +441,29 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
 {
     pl.brick = p->path == AC_PATH_BRICK;
     pl.comp = p->compensated != 0;
-    pl.G = p->lanes_per_contour ? p->lanes_per_contour : 32;
+    pl.acc = p->sampling == 1 || (p->sampling == 0 && p->N < 64);
+    if (pl.acc && !pl.comp) AC_FAIL(AC_ERR_ARG, "ac_evolve: accurate sampling is built with compensated sums only");
+    // lanes per contour: about 16 samples per lane, 8..32 lanes
+    int G = p->lanes_per_contour;
+    if (G == 0) {
+        G = 8;
+        while (G < 32 && (int64_t)G * 16 < p->N) G *= 2;
+    }
+    pl.G = G;
     pl.warps = p->warps_per_block ? p->warps_per_block : 8;
+    pl.quad_off = 0;
     if (!pl.brick) return AC_OK;
     const int al = 16 / vol->es;
     const int64_t budget = 200 * 1024;
     int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
     for (int d = 0; d < vol->ndim; ++d) {
-        const double cells = vol->ndim == 3 ? 2.0 : 4.0;
+        const double cells = vol->ndim == 3 ? 2.0 : 8.0;
         B[d] = p->brick[d] ? p->brick[d] : (int)std::lround(cells * stride_hint / vol->sp[d]);
         B[d] = std::max(1, std::min(B[d], (int)std::min<int64_t>(vol->n[d], 224)));
         h[d] = (int)std::ceil((2.5 * r_hint + 0.5 * p->dR) / vol->sp[d]) + 2;
     }
     for (int iter = 0; iter < 4096; ++iter) {
-        int64_t smem = vol->es;
+        int64_t raw = vol->es;
         bool fits_box = true;
         for (int d = 0; d < 3; ++d) {
             int ext = 1;
@@ -462,10 +478,24 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
             pl.ext[d] = ext;
             pl.B[d] = B[d];
             pl.halo[d] = h[d];
-            smem *= ext;
+            raw *= ext;
         }
-        if (fits_box && smem <= budget) {
-            pl.smem = (int)smem;
+        int64_t quad_off = 0, total = raw;
+        if (vol->ndim == 2) {   // float4 quads after the raw region
+            quad_off = (raw + 127) / 128 * 128;
+            total = quad_off + (int64_t)(pl.ext[0] - 1) * (pl.ext[1] - 1) * 16;
+        }
+        if (fits_box && total <= budget) {
+            pl.raw = (int)raw;
+            pl.quad_off = (int)quad_off;
+            pl.smem = (int)total;
+            if (p->warps_per_block == 0) {
+                // enough groups for the contours of a brick (lattice estimate), 2..8 warps
+                double per = 1.0;
+                for (int d = 0; d < vol->ndim; ++d) per *= std::max(1.0, B[d] * (double)vol->sp[d] / stride_hint);
+                const int w = (int)std::ceil(per * G / 32.0);
+                pl.warps = std::max(2, std::min(16, w));
+            }
             return AC_OK;
         }
         int hmax = 0, bmax = 0;
@@ -516,7 +546,7 @@ CUtensorMapDataType tma_type(ac_dtype t)
     }
 }
 
-VolDesc make_desc(const ac_contours *c, uint64_t seed)
+VolDesc make_desc(const ac_contours *c, uint32_t stream)
 {
     const ac_volume *v = c->vol;
     VolDesc d;
@@ -533,23 +563,22 @@ VolDesc make_desc(const ac_contours *c, uint64_t seed)
     d.scale = v->scale;
     d.state = c->state;
     d.C = c->C;
-    d.key0 = (uint32_t)seed;
-    d.key1 = (uint32_t)(seed >> 32);
+    d.stream = stream;
     return d;
 }
 
 cudaError_t launch_evolve(ac_dtype t, const EvolveArgs &a, const Plan &pl, int64_t grid, cudaStream_t st)
 {
     switch (t) {
-    case AC_U8: return launch_evolve_u8(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
-    case AC_U16: return launch_evolve_u16(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
-    case AC_F16: return launch_evolve_f16(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
-    default: return launch_evolve_f32(a, pl.brick, pl.G, pl.comp, pl.warps, grid, st);
+    case AC_U8: return launch_evolve_u8(a, pl.brick, pl.G, pl.comp, pl.acc, pl.warps, grid, st);
+    case AC_U16: return launch_evolve_u16(a, pl.brick, pl.G, pl.comp, pl.acc, pl.warps, grid, st);
+    case AC_F16: return launch_evolve_f16(a, pl.brick, pl.G, pl.comp, pl.acc, pl.warps, grid, st);
+    default: return launch_evolve_f32(a, pl.brick, pl.G, pl.comp, pl.acc, pl.warps, grid, st);
     }
 }
 
 // Shared by ac_evolve and ac_evolve_batch.  sets[0] owns the scratch buffers.
-ac_status evolve_sets(ac_contours *const *sets, const uint64_t *seeds, int n_sets, const ac_evolve_params *p,
+ac_status evolve_sets(ac_contours *const *sets, const uint32_t *streams, int n_sets, const ac_evolve_params *p,
                       const ac_trace *trace, cudaStream_t st)
 {
     ac_status s = check_params(p);
@@ -577,16 +606,37 @@ ac_status evolve_sets(ac_contours *const *sets, const uint64_t *seeds, int n_set
     a.total_contours = total;
     a.N = p->N;
     a.T = p->T;
-    a.stream_id = p->stream_id;
     a.first_iter = p->first_iter ? p->first_iter : 1;
     a.last_iter = a.first_iter + p->T - 1;
     a.update_last = p->update_last ? 1 : 0;
-    a.eps0 = p->eps0;
-    a.dR = p->dR;
-    a.Rmin = p->Rmin;
-    a.Rmax = p->Rmax;
-    a.max_step = p->max_step;
+    {
+        // Philox round keys and the weight-band constants of Eq. 5 (launch constants)
+        uint32_t k0 = (uint32_t)p->seed, k1 = (uint32_t)(p->seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            a.rk0[r] = k0;
+            a.rk1[r] = k1;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const int d = v0->ndim;
+        const double rho = std::pow(2.0, -1.0 / d), dR = p->dR, dr = rho * dR;
+        a.dR = p->dR;
+        a.Rmin = p->Rmin;
+        a.Rmax = p->Rmax;
+        a.half_eps0 = (float)(0.5 * p->eps0);
+        a.max_step = p->max_step;
+        a.max_step2 = (float)((double)p->max_step * p->max_step);
+        a.rho = (float)rho;
+        a.inv_dr = (float)(1.0 / dr);
+        a.inv_dR = (float)(1.0 / dR);
+        a.kR1 = (float)(-2.0 * rho / dr);
+        a.kR2 = (float)(1.0 / dR);
+        a.kr1 = (float)(-2.0 / dr);
+        a.kr2 = (float)(1.0 / dR);
+        a.vol_coef = (float)((d == 3 ? 4.0 / 3.0 * M_PI : M_PI) / p->N);
+    }
     a.status = sets[0]->status;
+    a.path_counts = sets[0]->path_counts;
     if (trace && trace->device_buf) {
         if (n_sets != 1) AC_FAIL(AC_ERR_ARG, "ac_evolve: trace is supported for a single set");
         if (trace->k_begin < 0 || trace->k_end > sets[0]->C || trace->k_begin > trace->k_end || trace->t_begin < 1 ||
@@ -604,7 +654,7 @@ ac_status evolve_sets(ac_contours *const *sets, const uint64_t *seeds, int n_set
     std::vector<VolDesc> desc(n_sets);
     int64_t bricks = 0, cbase = 0;
     for (int i = 0; i < n_sets; ++i) {
-        desc[i] = make_desc(sets[i], seeds ? seeds[i] : p->seed);
+        desc[i] = make_desc(sets[i], streams ? streams[i] : p->stream_id);
         desc[i].contour_base = cbase;
         cbase += sets[i]->C;
         if (pl.brick) {
@@ -623,6 +673,7 @@ ac_status evolve_sets(ac_contours *const *sets, const uint64_t *seeds, int n_set
     a.vols = sc.desc.as<VolDesc>();
 
     ac_contours *owner = sets[0];
+    AC_CUDA(cudaMemsetAsync(owner->path_counts, 0, sizeof(unsigned long long) * 3, st));
     if (!owner->ev0) {
         AC_CUDA(cudaEventCreate(&owner->ev0));
         AC_CUDA(cudaEventCreate(&owner->ev1));
@@ -691,6 +742,8 @@ ac_status evolve_sets(ac_contours *const *sets, const uint64_t *seeds, int n_set
         a.halo[d] = pl.halo[d];
         a.ext[d] = pl.ext[d];
     }
+    a.raw_bytes = pl.raw;
+    a.quad_off = pl.quad_off;
     a.smem_bytes = pl.smem;
     AC_CUDA(cudaEventRecord(owner->ev0, st));
     cudaError_t e = launch_evolve(v0->dtype, a, pl, bricks, st);
@@ -711,12 +764,23 @@ extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params,
     return evolve_sets(&ctr, nullptr, 1, params, trace, (cudaStream_t)cuda_stream);
 }
 
-extern "C" ac_status ac_evolve_batch(ac_contours *const *sets, const uint64_t *seeds, int32_t n_sets,
+extern "C" ac_status ac_evolve_batch(ac_contours *const *sets, const uint32_t *stream_ids, int32_t n_sets,
                                      const ac_evolve_params *params, void *cuda_stream)
 {
     g_err.clear();
     if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: need 1..4096 sets");
-    return evolve_sets(sets, seeds, n_sets, params, nullptr, (cudaStream_t)cuda_stream);
+    return evolve_sets(sets, stream_ids, n_sets, params, nullptr, (cudaStream_t)cuda_stream);
+}
+
+extern "C" ac_status ac_evolve_stats(ac_contours *ctr, int64_t counts[3], void *cuda_stream)
+{
+    g_err.clear();
+    if (!ctr || !counts) AC_FAIL(AC_ERR_ARG, "ac_evolve_stats: NULL argument");
+    unsigned long long c[3];
+    AC_CUDA(cudaMemcpyAsync(c, ctr->path_counts, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream));
+    AC_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    for (int i = 0; i < 3; ++i) counts[i] = (int64_t)c[i];
+    return AC_OK;
 }
 
 extern "C" ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms)

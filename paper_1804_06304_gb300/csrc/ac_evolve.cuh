@@ -2,6 +2,11 @@
 // Included once per voxel type by ac_evolve_<type>.cu so the instantiations
 // compile in parallel.  Method: arXiv:1804.06304, Eqs. 5-15 and the
 // "Monte-Carlo Integration" / "Parallel Contour Evaluation" sections.
+//
+// Every path (brick fast path, brick clamped path, global fallback, plain
+// one-launch-per-iteration kernel) shares the sample generation, weights,
+// accumulation, reduction and update below, and the gathers differ only in where
+// the voxels come from; the paths therefore give bit-identical results.
 #pragma once
 
 #include "ac_internal.cuh"
@@ -57,126 +62,234 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// ----------------------------------------------------------------- gathers
-// Staged region in shared memory: dense [ez][ey][ex] elements.
-template <typename T> struct SmemGather {
-    const T *p;
-    int py, pz;       // region pitches in elements
-    int ox, oy, oz;   // centre voxel relative to the region origin
+// ----------------------------------------------------------------- per contour-iteration
+// Samples use a raw radius variable rv (2D: sqrt of a 24-bit integer, in [0, 2^12);
+// 3D: cbrt of a uniform, in [0, 1)) and a raw direction (2D: (cos a, sin a) with
+// a = 2 pi u - pi, i.e. minus the unit direction; 3D: (s cos a, s sin a, cos phi)
+// with s = sin(phi)/2, i.e. (-dx/2, -dy/2, dz)).  The factors that turn them into
+// physical distance and index offsets are folded into these constants.
+template <int DIM> struct IterC {
+    AxisSplit ax[3];
+    float A1, B1;   // inner band coordinate t1 + 1/2 = rv A1 + B1
+    float A2, B2;   // outer band coordinate t2 + 1/2 = rv A2 + B2
+    float K[3];     // index offset along axis d = rv * K[d] * raw direction[d]
+};
 
-    template <int DIM>
-    __device__ __forceinline__ float at(int bx, int by, int bz, float fx, float fy, float fz) const
+template <int DIM>
+__device__ __forceinline__ void iter_consts(IterC<DIM> &ic, const float *c, float R, const VolDesc &V,
+                                            const EvolveArgs &a)
+{
+    const float Ro = R + 0.5f * a.dR;                         // radius of K (Eq. 5)
+    const float rs = DIM == 2 ? Ro * (1.0f / 4096.0f) : Ro;   // physical distance per unit rv
+    ic.A1 = rs * a.inv_dr;
+    ic.B1 = fmaf(-a.rho * R, a.inv_dr, 0.5f);
+    ic.A2 = rs * a.inv_dR;
+    ic.B2 = fmaf(-R, a.inv_dR, 0.5f);
+    const float fxy = DIM == 3 ? -2.0f : -1.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d < DIM) ic.ax[d] = split_axis(c[d], V.sp[d], V.inv_sp[d], V.n[d]);
+        ic.K[d] = (d < 2 ? fxy : 1.0f) * rs * V.inv_sp[d];
+    }
+}
+
+// ----------------------------------------------------------------- gathers
+// Coordinates x[d] arrive relative to the centre voxel ci (x = cf + offset).
+
+// Fast path: every tap of the ball lies inside the volume and the staged region,
+// so no clamping; floor and index come from one add rounded toward minus infinity
+// onto 2^23 + (ci - region origin).
+__device__ __forceinline__ void fast_axis(float x, float M, int &idx, float &fr)
+{
+    const float t = add_rd(x, M);
+    fr = x - (t - M);
+    idx = (int)__float_as_uint(t) - 0x4B000000;
+}
+
+// 2D region as float4 quads (v[y][x], v[y][x+1], v[y+1][x], v[y+1][x+1]).
+struct QuadFast {
+    const float4 *Q;
+    int qp;          // quads per row
+    float M[2];
+    __device__ __forceinline__ float at(float x0, float x1, float) const
     {
-        const T *q = p + (ox + bx) + (oy + by) * py + (DIM == 3 ? (oz + bz) * pz : 0);
-        const float v00 = to_f<T>(q[0]), v10 = to_f<T>(q[1]);
-        const float v01 = to_f<T>(q[py]), v11 = to_f<T>(q[py + 1]);
-        const float a0 = fmaf(fx, v10 - v00, v00), a1 = fmaf(fx, v11 - v01, v01);
-        const float s0 = fmaf(fy, a1 - a0, a0);
-        if (DIM == 2) return s0;
-        const T *r = q + pz;
-        const float w00 = to_f<T>(r[0]), w10 = to_f<T>(r[1]);
-        const float w01 = to_f<T>(r[py]), w11 = to_f<T>(r[py + 1]);
-        const float b0 = fmaf(fx, w10 - w00, w00), b1 = fmaf(fx, w11 - w01, w01);
-        const float s1 = fmaf(fy, b1 - b0, b0);
-        return fmaf(fz, s1 - s0, s0);
+        int i0, i1;
+        float f0, f1;
+        fast_axis(x0, M[0], i0, f0);
+        fast_axis(x1, M[1], i1, f1);
+        const float4 q = Q[i1 * qp + i0];
+        const float a0 = fmaf(f0, q.y - q.x, q.x), a1 = fmaf(f0, q.w - q.z, q.z);
+        return fmaf(f1, a1 - a0, a0);
     }
 };
 
-// The row-pitched volume in global memory (read-only path).
-template <typename T> struct GlobalGather {
+// Bilinear / trilinear from four / eight taps of a raw array at q.
+template <int DIM, typename T, typename LD>
+__device__ __forceinline__ float interp(const T *q, int64_t py, int64_t pz, float f0, float f1, float f2, LD ld)
+{
+    const float v00 = ld(q), v10 = ld(q + 1), v01 = ld(q + py), v11 = ld(q + py + 1);
+    const float a0 = fmaf(f0, v10 - v00, v00), a1 = fmaf(f0, v11 - v01, v01);
+    const float s0 = fmaf(f1, a1 - a0, a0);
+    if (DIM == 2) return s0;
+    const T *r = q + pz;
+    const float w00 = ld(r), w10 = ld(r + 1), w01 = ld(r + py), w11 = ld(r + py + 1);
+    const float b0 = fmaf(f0, w10 - w00, w00), b1 = fmaf(f0, w11 - w01, w01);
+    const float s1 = fmaf(f1, b1 - b0, b0);
+    return fmaf(f2, s1 - s0, s0);
+}
+
+template <typename T> struct SmemLoad {
+    __device__ __forceinline__ float operator()(const T *p) const { return to_f<T>(*p); }
+};
+template <typename T> struct GlobalLoad {
+    __device__ __forceinline__ float operator()(const T *p) const { return ldg_f<T>(p); }
+};
+
+template <int DIM, typename T> struct RawFast {
+    const T *p;
+    int py, pz;
+    float M[3];
+    __device__ __forceinline__ float at(float x0, float x1, float x2) const
+    {
+        int i0, i1, i2 = 0;
+        float f0, f1, f2 = 0.0f;
+        fast_axis(x0, M[0], i0, f0);
+        fast_axis(x1, M[1], i1, f1);
+        if (DIM == 3) fast_axis(x2, M[2], i2, f2);
+        return interp<DIM, T>(p + i0 + i1 * py + i2 * pz, py, pz, f0, f1, f2, SmemLoad<T>());
+    }
+};
+
+// Clamped path in shared memory (quads in 2D, raw voxels otherwise).
+template <int DIM, typename T, bool QUAD> struct SmemClamp {
+    const void *p;
+    int py, pz;      // raw pitches, or quads per row in py
+    AxisSplit ax[3];
+    int o[3];        // centre voxel relative to the region origin
+    __device__ __forceinline__ float at(float x0, float x1, float x2) const
+    {
+        int b0, b1, b2 = 0;
+        float f0, f1, f2 = 0.0f;
+        axis_tap(ax[0], x0, b0, f0);
+        axis_tap(ax[1], x1, b1, f1);
+        if (DIM == 3) axis_tap(ax[2], x2, b2, f2);
+        if (QUAD) {
+            const float4 q = reinterpret_cast<const float4 *>(p)[(o[1] + b1) * py + (o[0] + b0)];
+            const float a0 = fmaf(f0, q.y - q.x, q.x), a1 = fmaf(f0, q.w - q.z, q.z);
+            return fmaf(f1, a1 - a0, a0);
+        }
+        const T *q = reinterpret_cast<const T *>(p) + (o[0] + b0) + (o[1] + b1) * py + (DIM == 3 ? (o[2] + b2) * pz : 0);
+        return interp<DIM, T>(q, py, pz, f0, f1, f2, SmemLoad<T>());
+    }
+};
+
+// Clamped path from the row-pitched volume in global memory.
+template <int DIM, typename T> struct GlobalClamp {
     const T *p;
     int64_t py, pz;
-    int ci, cj, ck;   // centre voxel
-
-    template <int DIM>
-    __device__ __forceinline__ float at(int bx, int by, int bz, float fx, float fy, float fz) const
+    AxisSplit ax[3];
+    __device__ __forceinline__ float at(float x0, float x1, float x2) const
     {
-        const T *q = p + (int64_t)(ci + bx) + (int64_t)(cj + by) * py + (DIM == 3 ? (int64_t)(ck + bz) * pz : 0);
-        const float v00 = ldg_f<T>(q), v10 = ldg_f<T>(q + 1);
-        const float v01 = ldg_f<T>(q + py), v11 = ldg_f<T>(q + py + 1);
-        const float a0 = fmaf(fx, v10 - v00, v00), a1 = fmaf(fx, v11 - v01, v01);
-        const float s0 = fmaf(fy, a1 - a0, a0);
-        if (DIM == 2) return s0;
-        const T *r = q + pz;
-        const float w00 = ldg_f<T>(r), w10 = ldg_f<T>(r + 1);
-        const float w01 = ldg_f<T>(r + py), w11 = ldg_f<T>(r + py + 1);
-        const float b0 = fmaf(fx, w10 - w00, w00), b1 = fmaf(fx, w11 - w01, w01);
-        const float s1 = fmaf(fy, b1 - b0, b0);
-        return fmaf(fz, s1 - s0, s0);
+        int b0, b1, b2 = 0;
+        float f0, f1, f2 = 0.0f;
+        axis_tap(ax[0], x0, b0, f0);
+        axis_tap(ax[1], x1, b1, f1);
+        if (DIM == 3) axis_tap(ax[2], x2, b2, f2);
+        const T *q = p + (int64_t)(ax[0].ci + b0) + (int64_t)(ax[1].ci + b1) * py +
+                     (DIM == 3 ? (int64_t)(ax[2].ci + b2) * pz : 0);
+        return interp<DIM, T>(q, py, pz, f0, f1, f2, GlobalLoad<T>());
     }
 };
 
 // ----------------------------------------------------------------- one sample
-// Adds the sample at distance r along unit direction dir to the five sums
-// J = sum S I, J_R = sum dS/dR I, J_c = sum -S'(r) dir I (Eqs. 5, 7-10).
-template <int DIM, bool COMP, typename Gather>
-__device__ __forceinline__ void add_sample(const Gather &gat, const AxisSplit *ax, const float *inv_sp,
-                                           const WeightConsts &W, float r, float dx, float dy, float dz,
-                                           KSum *acc)
+// Weights of Eq. 5 (four regions; linear bands of widths dr and dR) and the five
+// sums J = sum S I, J_R = sum dS/dR I, J_c = sum -S'(r) (raw direction) I.
+template <int DIM, bool COMP>
+__device__ __forceinline__ void accumulate(const IterC<DIM> &ic, const EvolveArgs &a, float rv, float I, float d0,
+                                           float d1, float d2, KSum *acc)
 {
-    int bx, by, bz = 0;
-    float fx, fy, fz = 0.0f;
-    axis_tap(ax[0], r * dx * inv_sp[0], bx, fx);
-    axis_tap(ax[1], r * dy * inv_sp[1], by, fy);
-    if (DIM == 3) axis_tap(ax[2], r * dz * inv_sp[2], bz, fz);
-    const float I = gat.template at<DIM>(bx, by, bz, fx, fy, fz);
-
-    const float t1 = fmaf(r, W.a1, W.b1), t2 = fmaf(r, W.a2, W.b2);
-    const float S = fmaf(2.0f, __saturatef(t1), -1.0f) - __saturatef(t2);
-    const float in1 = (t1 >= 0.0f && t1 < 1.0f) ? 1.0f : 0.0f;
-    const float in2 = (t2 >= 0.0f && t2 < 1.0f) ? 1.0f : 0.0f;
-    const float dSdR = fmaf(in1, W.kR1, in2 * W.kR2);
-    const float g = fmaf(in1, W.kr1, in2 * W.kr2) * I;   // -S'(r) I
+    const float t1 = fmaf(rv, ic.A1, ic.B1), t2 = fmaf(rv, ic.A2, ic.B2);
+    const float r1 = __saturatef(t1), r2 = __saturatef(t2);
+    const float S = fmaf(2.0f, r1, -1.0f) - r2;
+    const bool b1 = r1 == t1, b2 = r2 == t2;   // sample inside the inner / outer band
+    const float dSdR = (b1 ? a.kR1 : 0.0f) + (b2 ? a.kR2 : 0.0f);
+    const float g = ((b1 ? a.kr1 : 0.0f) + (b2 ? a.kr2 : 0.0f)) * I;
     if (COMP) {
         kadd(acc[0], S * I);
         kadd(acc[1], dSdR * I);
-        kadd(acc[2], g * dx);
-        kadd(acc[3], g * dy);
-        if (DIM == 3) kadd(acc[4], g * dz);
+        kadd(acc[2], g * d0);
+        kadd(acc[3], g * d1);
+        if (DIM == 3) kadd(acc[4], g * d2);
     } else {
         acc[0].s = fmaf(S, I, acc[0].s);
         acc[1].s = fmaf(dSdR, I, acc[1].s);
-        acc[2].s = fmaf(g, dx, acc[2].s);
-        acc[3].s = fmaf(g, dy, acc[3].s);
-        if (DIM == 3) acc[4].s = fmaf(g, dz, acc[4].s);
+        acc[2].s = fmaf(g, d0, acc[2].s);
+        acc[3].s = fmaf(g, d1, acc[3].s);
+        if (DIM == 3) acc[4].s = fmaf(g, d2, acc[4].s);
     }
 }
 
 // All samples of one contour-iteration handled by this lane (lane `lig` of G).
 // 3D: sample j uses Philox block (j, n, k, stream): radius cbrt(u0), cos(phi) =
 // 1 - 2 u1, azimuth 2 pi u2.  2D: block m gives samples 2m and 2m+1, radius
-// sqrt(u), azimuth 2 pi u' ("Monte-Carlo Integration" section).
-template <int DIM, int G, bool COMP, typename Gather>
-__device__ __forceinline__ void sample_contour(const Gather &gat, const AxisSplit *ax, const float *inv_sp,
-                                               const WeightConsts &W, float Ro, int N, uint32_t n, uint32_t k,
-                                               uint32_t stream, uint32_t key0, uint32_t key1, int lig,
-                                               KSum *acc)
+// sqrt(u), azimuth 2 pi u' ("Monte-Carlo Integration" section).  ACC selects
+// correctly rounded sqrt / cbrt and the polynomial sine and cosine (used when few
+// samples make per-sample accuracy visible); otherwise the hardware
+// approximations.
+template <int DIM, bool ACC>
+__device__ __forceinline__ void raw_direction2(uint32_t wa, float &d0, float &d1)
 {
-    if (DIM == 3) {
+    if (ACC) {
+        neg_sincos_turn(wa >> 8, d0, d1);
+    } else {
+        constexpr float ANG = 6.283185307179586f / 16777216.0f;   // 2 pi / 2^24
+        const float ang = fmaf(top24(wa), ANG, -3.14159265358979323846f);
+        d0 = cos_approx(ang);
+        d1 = sin_approx(ang);
+    }
+}
+
+template <int DIM, int G, bool COMP, bool ACC, typename Gather>
+__device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a,
+                                               uint32_t n, uint32_t k, uint32_t stream, int lig, KSum *acc)
+{
+    if constexpr (DIM == 3) {
 #pragma unroll 2
-        for (int j = lig; j < N; j += G) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)j, n, k, stream), key0, key1);
-            const float u1 = u24(w.y);
-            const float rad = cbrtf(u24(w.x));
-            const float cphi = fmaf(-2.0f, u1, 1.0f);
-            const float sphi = 2.0f * sqrtf(u1 * (1.0f - u1));
-            float sn, cs;
-            sincospif(2.0f * u24(w.z), &sn, &cs);
-            add_sample<3, COMP>(gat, ax, inv_sp, W, Ro * rad, sphi * cs, sphi * sn, cphi, acc);
+        for (int j = lig; j < a.N; j += G) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)j, n, k, stream), a.rk0, a.rk1);
+            const float u0 = top24(w.x) * 5.9604644775390625e-8f;
+            const float rv = ACC ? cbrtf(u0) : ex2_approx(lg2_approx(u0) * (1.0f / 3.0f));
+            const float t = top24(w.y) * 5.9604644775390625e-8f;
+            const float cphi = fmaf(-2.0f, t, 1.0f);
+            const float sh = ACC ? sqrtf(t * (1.0f - t)) : sqrt_approx(t * (1.0f - t));
+            float c0, s0;
+            raw_direction2<DIM, ACC>(w.z, c0, s0);
+            const float d0 = sh * c0, d1 = sh * s0;
+            const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
+            const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
+            const float x2 = fmaf(rv * ic.K[2], cphi, ic.ax[2].cf);
+            accumulate<DIM, COMP>(ic, a, rv, gat.at(x0, x1, x2), d0, d1, cphi, acc);
         }
     } else {
-        const int blocks = (N + 1) >> 1;
+        const int blocks = (a.N + 1) >> 1;
+#pragma unroll 2
         for (int m = lig; m < blocks; m += G) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), key0, key1);
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
             {
-                float sn, cs;
-                sincospif(2.0f * u24(w.y), &sn, &cs);
-                add_sample<2, COMP>(gat, ax, inv_sp, W, Ro * sqrtf(u24(w.x)), cs, sn, 0.0f, acc);
+                const float rv = ACC ? sqrtf(top24(w.x)) : sqrt_approx(top24(w.x));
+                float d0, d1;
+                raw_direction2<DIM, ACC>(w.y, d0, d1);
+                const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
+                const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
+                accumulate<DIM, COMP>(ic, a, rv, gat.at(x0, x1, 0.0f), d0, d1, 0.0f, acc);
             }
-            if (2 * m + 1 < N) {
-                float sn, cs;
-                sincospif(2.0f * u24(w.w), &sn, &cs);
-                add_sample<2, COMP>(gat, ax, inv_sp, W, Ro * sqrtf(u24(w.z)), cs, sn, 0.0f, acc);
+            if (2 * m + 1 < a.N) {
+                const float rv = ACC ? sqrtf(top24(w.z)) : sqrt_approx(top24(w.z));
+                float d0, d1;
+                raw_direction2<DIM, ACC>(w.w, d0, d1);
+                const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
+                const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
+                accumulate<DIM, COMP>(ic, a, rv, gat.at(x0, x1, 0.0f), d0, d1, 0.0f, acc);
             }
         }
     }
@@ -189,19 +302,20 @@ struct Step {
 
 // Sums to energy and gradient (Eqs. 5-11, centre/radius form).
 template <int DIM>
-__device__ __forceinline__ Step finish(const float *sums, float R, float dR, int N, float scale)
+__device__ __forceinline__ Step finish(const float *sums, float R, const EvolveArgs &a, float scale)
 {
-    const float Ro = R + 0.5f * dR;
-    const float V = DIM == 3 ? 4.18879020478639098461f * Ro * Ro * Ro : 3.14159265358979323846f * Ro * Ro;
-    const float wmc = V / (float)N * scale;
-    const float twoR = 2.0f * R;
-    const float inv = DIM == 3 ? 1.0f / (twoR * twoR * twoR) : 1.0f / (twoR * twoR);
+    const float Ro = R + 0.5f * a.dR;
+    const float RoD = DIM == 3 ? Ro * Ro * Ro : Ro * Ro;
+    const float wmc = a.vol_coef * RoD * scale;                 // (V / N) x intensity scale
+    const float inv2R = __frcp_rn(2.0f * R);
+    const float inv = DIM == 3 ? inv2R * inv2R * inv2R : inv2R * inv2R;   // (2R)^-d
+    const float fxy = DIM == 3 ? -2.0f : -1.0f;                 // raw direction to unit direction
     Step s;
     const float J = sums[0] * wmc;
     s.E = J * inv;
-    s.dEdR = (sums[1] * wmc - (float)DIM * J / R) * inv;
-    s.g[0] = sums[2] * wmc * inv;
-    s.g[1] = sums[3] * wmc * inv;
+    s.dEdR = (sums[1] * wmc - (float)DIM * 2.0f * J * inv2R) * inv;
+    s.g[0] = fxy * sums[2] * wmc * inv;
+    s.g[1] = fxy * sums[3] * wmc * inv;
     s.g[2] = DIM == 3 ? sums[4] * wmc * inv : 0.0f;
     return s;
 }
@@ -212,11 +326,11 @@ template <int DIM>
 __device__ __forceinline__ void update(const Step &s, int n, const EvolveArgs &a, const float *box_hi, float *c,
                                        float &R)
 {
-    const float eta = 0.5f * a.eps0 / sqrtf((float)n);
+    const float eta = a.half_eps0 * rsqrt_approx((float)n);
     float d[3] = {-eta * s.g[0], -eta * s.g[1], DIM == 3 ? -eta * s.g[2] : 0.0f};
-    const float nrm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    if (nrm > a.max_step) {
-        const float f = a.max_step / nrm;
+    const float nrm2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (nrm2 > a.max_step2) {
+        const float f = a.max_step * rsqrt_approx(nrm2);
         d[0] *= f;
         d[1] *= f;
         d[2] *= f;
@@ -225,6 +339,13 @@ __device__ __forceinline__ void update(const Step &s, int n, const EvolveArgs &a
     R = fminf(fmaxf(R + dRr, a.Rmin), a.Rmax);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) c[i] = fminf(fmaxf(c[i] + d[i], 0.0f), box_hi[i]);
+}
+
+// A non-finite evaluation (non-finite voxels) freezes the contour and is reported
+// through the status word rather than pushed through the clamps.
+__device__ __forceinline__ bool finite_step(const Step &s)
+{
+    return isfinite(s.E) && isfinite(s.dEdR) && isfinite(s.g[0]) && isfinite(s.g[1]) && isfinite(s.g[2]);
 }
 
 __device__ __forceinline__ void write_trace(const EvolveArgs &a, int vol, int64_t k, int n, const float *c, float R,
@@ -244,19 +365,16 @@ template <int G> __device__ __forceinline__ unsigned group_mask()
 }
 
 // Evaluate one contour-iteration with the chosen gather, reduce over the group.
-template <int DIM, int G, bool COMP, typename Gather>
-__device__ __forceinline__ Step eval_contour(const Gather &gat, const AxisSplit *ax, const float *inv_sp,
-                                             float R, const EvolveArgs &a, int n, uint32_t k, uint32_t key0,
-                                             uint32_t key1, float scale, int lig, unsigned mask)
+template <int DIM, int G, bool COMP, bool ACC, typename Gather>
+__device__ __forceinline__ Step eval_contour(const Gather &gat, const IterC<DIM> &ic, float R, const EvolveArgs &a,
+                                             int n, uint32_t k, uint32_t stream, float scale, int lig, unsigned mask)
 {
-    const float Ro = R + 0.5f * a.dR;
-    const WeightConsts W = weight_consts(R, a.dR, DIM);
     KSum acc[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    sample_contour<DIM, G, COMP>(gat, ax, inv_sp, W, Ro, a.N, (uint32_t)n, k, a.stream_id, key0, key1, lig, acc);
+    sample_contour<DIM, G, COMP, ACC>(gat, ic, a, (uint32_t)n, k, stream, lig, acc);
     float sums[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) sums[i] = (DIM == 2 && i == 4) ? 0.0f : group_reduce<G, COMP>(acc[i], mask);
-    return finish<DIM>(sums, R, a.dR, a.N, scale);
+    return finish<DIM>(sums, R, a, scale);
 }
 
 __device__ __forceinline__ int find_vol(const EvolveArgs &a, int64_t idx, bool by_brick)
@@ -278,16 +396,19 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *keys, int64_t
 }
 
 // ----------------------------------------------------------------- brick kernel
-// One CTA per brick: TMA stages the brick plus halo into shared memory once; each
-// group of G lanes then evolves one contour of the brick through all T iterations
+// One CTA per brick: TMA stages the brick plus halo into shared memory once (2D:
+// then rewritten as float4 quads so one 128-bit load feeds a bilinear sample);
+// each group of G lanes evolves one contour of the brick through all iterations
 // with its state in registers ("Parallel Contour Evaluation": lanes share the
-// samples of a contour).  A contour whose ball leaves the staged region gathers
-// from global memory for that iteration (the branch is uniform per group).
-template <int DIM, typename T, int G, bool COMP>
-__global__ void __launch_bounds__(256) evolve_brick_kernel(const EvolveArgs a)
+// samples of a contour).  Per iteration a group takes the fast path (ball inside
+// the volume and the region), the clamped shared-memory path (ball crosses the
+// volume border) or, when the ball has left the region, global-memory gathers.
+template <int DIM, typename T, int G, bool COMP, bool ACC>
+__global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant__ EvolveArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ unsigned int s_paths[3];
 
     const int64_t b = blockIdx.x;
     const int64_t cb = lower_bound_u32(a.sorted_brick, a.total_contours, (uint32_t)b);
@@ -302,25 +423,38 @@ __global__ void __launch_bounds__(256) evolve_brick_kernel(const EvolveArgs a)
     const int bzi = (int)(lb / ((int64_t)V.nb[0] * V.nb[1]));
     // region origin: max(0, brick - halo), x rounded down to the 16-byte TMA alignment
     constexpr int AL = 16 / (int)sizeof(T);
-    const int r0x = max(0, bxi * a.B[0] - a.halo[0]) / AL * AL;
-    const int r0y = max(0, byi * a.B[1] - a.halo[1]);
-    const int r0z = DIM == 3 ? max(0, bzi * a.B[2] - a.halo[2]) : 0;
+    const int r0[3] = {max(0, bxi * a.B[0] - a.halo[0]) / AL * AL, max(0, byi * a.B[1] - a.halo[1]),
+                       DIM == 3 ? max(0, bzi * a.B[2] - a.halo[2]) : 0};
 
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        s_paths[0] = s_paths[1] = s_paths[2] = 0;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&mbar, (uint32_t)a.smem_bytes);
-        tma_load_3d(smem_raw, &a.tmaps[v], r0x, r0y, r0z, &mbar);
+        mbar_expect_tx(&mbar, (uint32_t)a.raw_bytes);
+        tma_load_3d(smem_raw, &a.tmaps[v], r0[0], r0[1], r0[2], &mbar);
     }
     if (!mbar_wait_bounded(&mbar, 0, 1u << 22)) {
         if (threadIdx.x == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
         mbar_wait_bounded(&mbar, 0, 1u << 22);   // let an in-flight copy land before exit
         return;
     }
-
     const T *reg = reinterpret_cast<const T *>(smem_raw);
+    const bool quad = DIM == 2 && a.quad_off > 0;
+    float4 *Q = reinterpret_cast<float4 *>(smem_raw + a.quad_off);
+    const int qp = a.ext[0] - 1;
+    if (quad) {
+        const int nq = qp * (a.ext[1] - 1);
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            const int y = i / qp, x = i - y * qp;
+            const T *r = reg + y * a.ext[0] + x;
+            Q[i] = make_float4(to_f<T>(r[0]), to_f<T>(r[1]), to_f<T>(r[a.ext[0]]), to_f<T>(r[a.ext[0] + 1]));
+        }
+        __syncthreads();
+    }
+
     const int py = a.ext[0], pz = a.ext[0] * a.ext[1];
-    const float inv_sp[3] = {V.inv_sp[0], V.inv_sp[1], V.inv_sp[2]};
     const int lig = threadIdx.x % G;
     const int grp = threadIdx.x / G;
     const int ngrp = blockDim.x / G;
@@ -333,33 +467,51 @@ __global__ void __launch_bounds__(256) evolve_brick_kernel(const EvolveArgs a)
         float R = V.state[3 * C + k];
         Step s;
         for (int n = a.first_iter; n <= a.last_iter; ++n) {
-            AxisSplit ax[3];
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) ax[d] = split_axis(c[d], V.sp[d], inv_sp[d], V.n[d]);
-            // taps of the whole ball, clamped like the samples: inside the region?
+            IterC<DIM> ic;
+            iter_consts<DIM>(ic, c, R, V, a);
+            // where do the taps of the whole ball fall (clamped like the samples)?
             const float Ro = R + 0.5f * a.dR;
-            bool inside = true;
-            const int r0[3] = {r0x, r0y, r0z};
+            bool inside = true, interior = true;
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                const float e = fmaf(Ro, inv_sp[d], 1e-3f);
-                const float lo = fminf(fmaxf(ax[d].cf - e, ax[d].lo), ax[d].hi);
-                const float hi = fminf(fmaxf(ax[d].cf + e, ax[d].lo), ax[d].hi);
-                const int tlo = ax[d].ci + (int)fminf(floorf(lo), ax[d].top);
-                const int thi = ax[d].ci + (int)fminf(floorf(hi), ax[d].top) + 1;
+                const AxisSplit &x = ic.ax[d];
+                const float e = fmaf(Ro, V.inv_sp[d], 1e-3f);
+                interior = interior && (x.cf - e >= x.lo) && (x.cf + e < x.hi);
+                const float lo = fminf(fmaxf(x.cf - e, x.lo), x.hi);
+                const float hi = fminf(fmaxf(x.cf + e, x.lo), x.hi);
+                const int tlo = x.ci + (int)fminf(floorf(lo), x.top);
+                const int thi = x.ci + (int)fminf(floorf(hi), x.top) + 1;
                 inside = inside && tlo >= r0[d] && thi < r0[d] + a.ext[d];
             }
-            if (inside) {
-                SmemGather<T> gat{reg, py, pz, ax[0].ci - r0x, ax[1].ci - r0y, DIM == 3 ? ax[2].ci - r0z : 0};
-                s = eval_contour<DIM, G, COMP>(gat, ax, inv_sp, R, a, n, (uint32_t)k, V.key0, V.key1, V.scale,
-                                               lig, mask);
+            const int o[3] = {ic.ax[0].ci - r0[0], ic.ax[1].ci - r0[1], DIM == 3 ? ic.ax[2].ci - r0[2] : 0};
+            if (lig == 0) atomicAdd_block(&s_paths[inside ? (interior ? 0 : 1) : 2], 1u);
+            if (inside && interior) {
+                const float M[3] = {8388608.0f + (float)o[0], 8388608.0f + (float)o[1], 8388608.0f + (float)o[2]};
+                if (quad) {
+                    QuadFast gat{Q, qp, {M[0], M[1]}};
+                    s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
+                } else {
+                    RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}};
+                    s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
+                }
+            } else if (inside) {
+                if (quad) {
+                    SmemClamp<DIM, T, true> gat{Q, qp, 0, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]}};
+                    s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
+                } else {
+                    SmemClamp<DIM, T, false> gat{reg, py, pz, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]}};
+                    s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
+                }
             } else {
-                GlobalGather<T> gat{reinterpret_cast<const T *>(V.data), V.pitch_y, V.pitch_z, ax[0].ci, ax[1].ci,
-                                    DIM == 3 ? ax[2].ci : 0};
-                s = eval_contour<DIM, G, COMP>(gat, ax, inv_sp, R, a, n, (uint32_t)k, V.key0, V.key1, V.scale,
-                                               lig, mask);
+                GlobalClamp<DIM, T> gat{reinterpret_cast<const T *>(V.data), V.pitch_y, V.pitch_z,
+                                        {ic.ax[0], ic.ax[1], ic.ax[2]}};
+                s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
             }
             if (lig == 0) write_trace(a, v, k, n, c, R, s);
+            if (!finite_step(s)) {
+                if (lig == 0) atomicOr(a.status, STATUS_NONFINITE);
+                break;
+            }
             if (n < a.last_iter || a.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
         }
         if (lig == 0) {
@@ -372,14 +524,19 @@ __global__ void __launch_bounds__(256) evolve_brick_kernel(const EvolveArgs a)
                 atomicOr(a.status, STATUS_NONFINITE);
         }
     }
+    __syncthreads();
+    if (threadIdx.x < 3 && s_paths[threadIdx.x]) atomicAdd(&a.path_counts[threadIdx.x], (unsigned long long)s_paths[threadIdx.x]);
 }
 
 // ----------------------------------------------------------------- plain kernel
 // One iteration (a.iter0) for every contour: state read from and written back to
 // global memory, samples gathered from the global volume.  Launched T times.
-template <int DIM, typename T, int G, bool COMP>
-__global__ void __launch_bounds__(256) evolve_plain_kernel(const EvolveArgs a)
+template <int DIM, typename T, int G, bool COMP, bool ACC>
+__global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant__ EvolveArgs a)
 {
+    __shared__ unsigned int s_glob;
+    if (threadIdx.x == 0) s_glob = 0;
+    __syncthreads();
     const int lig = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
@@ -391,17 +548,16 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const EvolveArgs a)
         const int64_t C = V.C;
         float c[3] = {V.state[k], V.state[C + k], DIM == 3 ? V.state[2 * C + k] : 0.0f};
         float R = V.state[3 * C + k];
-        const float inv_sp[3] = {V.inv_sp[0], V.inv_sp[1], V.inv_sp[2]};
-        AxisSplit ax[3];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) ax[d] = split_axis(c[d], V.sp[d], inv_sp[d], V.n[d]);
-        GlobalGather<T> gat{reinterpret_cast<const T *>(V.data), V.pitch_y, V.pitch_z, ax[0].ci, ax[1].ci,
-                            DIM == 3 ? ax[2].ci : 0};
-        const Step s = eval_contour<DIM, G, COMP>(gat, ax, inv_sp, R, a, n, (uint32_t)k, V.key0, V.key1, V.scale,
-                                                  lig, mask);
+        IterC<DIM> ic;
+        iter_consts<DIM>(ic, c, R, V, a);
+        GlobalClamp<DIM, T> gat{reinterpret_cast<const T *>(V.data), V.pitch_y, V.pitch_z,
+                                {ic.ax[0], ic.ax[1], ic.ax[2]}};
+        const Step s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
         if (lig == 0) {
+            atomicAdd_block(&s_glob, 1u);
             write_trace(a, v, k, n, c, R, s);
-            if (n < a.last_iter || a.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
+            if (!finite_step(s)) atomicOr(a.status, STATUS_NONFINITE);
+            else if (n < a.last_iter || a.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
             V.state[k] = c[0];
             V.state[C + k] = c[1];
             if (DIM == 3) V.state[2 * C + k] = c[2];
@@ -411,37 +567,42 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const EvolveArgs a)
                 atomicOr(a.status, STATUS_NONFINITE);
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_glob) atomicAdd(&a.path_counts[2], (unsigned long long)s_glob);
 }
 
 // ----------------------------------------------------------------- launchers
-template <int DIM, typename T, int G, bool COMP>
+template <int DIM, typename T, int G, bool COMP, bool ACC>
 cudaError_t launch_brick_t(const EvolveArgs &a, int warps, cudaStream_t st)
 {
-    auto kern = evolve_brick_kernel<DIM, T, G, COMP>;
+    auto kern = evolve_brick_kernel<DIM, T, G, COMP, ACC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)a.total_bricks, warps * 32, a.smem_bytes, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int DIM, typename T, int G, bool COMP>
+template <int DIM, typename T, int G, bool COMP, bool ACC>
 cudaError_t launch_plain_t(const EvolveArgs &a, int warps, int64_t grid, cudaStream_t st)
 {
-    evolve_plain_kernel<DIM, T, G, COMP><<<(unsigned)grid, warps * 32, 0, st>>>(a);
+    evolve_plain_kernel<DIM, T, G, COMP, ACC><<<(unsigned)grid, warps * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
+// Instantiated combinations: every lane count with compensated sums in the fast
+// and the accurate sampling mode, and plain FP32 sums in the fast mode.
 template <typename T>
-cudaError_t launch_evolve_t(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+cudaError_t launch_evolve_t(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                             cudaStream_t st)
 {
-#define AC_DISPATCH(DIM, GG, CC)                                                                    \
-    if (a.ndim == DIM && G == GG && comp == CC)                                                     \
-        return brick ? launch_brick_t<DIM, T, GG, CC>(a, warps, st) : launch_plain_t<DIM, T, GG, CC>(a, warps, grid, st);
-    AC_DISPATCH(3, 32, true) AC_DISPATCH(3, 16, true) AC_DISPATCH(3, 8, true)
-    AC_DISPATCH(3, 32, false) AC_DISPATCH(3, 16, false) AC_DISPATCH(3, 8, false)
-    AC_DISPATCH(2, 32, true) AC_DISPATCH(2, 16, true) AC_DISPATCH(2, 8, true)
-    AC_DISPATCH(2, 32, false) AC_DISPATCH(2, 16, false) AC_DISPATCH(2, 8, false)
+#define AC_DISPATCH(DIM, GG, CC, AA)                                                                \
+    if (a.ndim == DIM && G == GG && comp == CC && acc == AA)                                       \
+        return brick ? launch_brick_t<DIM, T, GG, CC, AA>(a, warps, st)                            \
+                     : launch_plain_t<DIM, T, GG, CC, AA>(a, warps, grid, st);
+#define AC_DISPATCH_G(DIM, CC, AA) AC_DISPATCH(DIM, 32, CC, AA) AC_DISPATCH(DIM, 16, CC, AA) AC_DISPATCH(DIM, 8, CC, AA)
+    AC_DISPATCH_G(3, true, false) AC_DISPATCH_G(3, false, false) AC_DISPATCH_G(3, true, true)
+    AC_DISPATCH_G(2, true, false) AC_DISPATCH_G(2, false, false) AC_DISPATCH_G(2, true, true)
+#undef AC_DISPATCH_G
 #undef AC_DISPATCH
     return cudaErrorInvalidValue;
 }

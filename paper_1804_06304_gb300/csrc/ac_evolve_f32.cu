@@ -3,9 +3,9 @@
 #include "ac_host.h"
 
 namespace ac {
-cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                              cudaStream_t st)
 {
-    return launch_evolve_t<float>(a, brick, G, comp, warps, grid, st);
+    return launch_evolve_t<float>(a, brick, G, comp, acc, warps, grid, st);
 }
 }  // namespace ac

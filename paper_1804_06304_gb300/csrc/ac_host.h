@@ -62,6 +62,7 @@ struct ac_contours {
     int64_t C;
     float *state;         // 5 x C
     int32_t *status;      // device status word
+    unsigned long long *path_counts;   // device [3]: contour-iterations per gather path
     double stride_hint;   // lattice stride (or mean spacing of explicit seeds)
     double r_hint;        // largest initial radius
     ac::Scratch scratch;
@@ -80,13 +81,13 @@ void set_error(const std::string &msg);
 // count of the library's own kernel launches
 void count_launch(int64_t n = 1);
 
-cudaError_t launch_evolve_u8(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+cudaError_t launch_evolve_u8(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                              cudaStream_t st);
-cudaError_t launch_evolve_u16(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+cudaError_t launch_evolve_u16(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                               cudaStream_t st);
-cudaError_t launch_evolve_f16(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+cudaError_t launch_evolve_f16(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                               cudaStream_t st);
-cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, int warps, int64_t grid,
+cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                               cudaStream_t st);
 
 // localization (ac_localize.cu); returns an ac_status and sets the message

@@ -34,7 +34,8 @@ struct VolDesc {
     int64_t C;           // contours in this set
     int64_t brick_base;  // first global brick index of this set
     int64_t contour_base;// first global contour index of this set
-    uint32_t key0, key1; // Philox key
+    uint32_t stream;     // fourth Philox counter word of this set
+    uint32_t pad_;
 };
 
 struct EvolveArgs {
@@ -47,27 +48,49 @@ struct EvolveArgs {
     int64_t total_contours;
     int64_t total_bricks;
     int32_t B[3];        // brick interior, voxels
-    int32_t halo[3];     // halo, voxels (x a multiple of the TMA alignment)
-    int32_t ext[3];      // staged region = B + 2 halo
-    int32_t smem_bytes;  // staged region bytes
+    int32_t halo[3];     // halo, voxels
+    int32_t ext[3];      // staged region extents
+    int32_t raw_bytes;   // staged region bytes (TMA box)
+    int32_t quad_off;    // 2D: byte offset of the float4 quad array (0: raw gathers)
+    int32_t smem_bytes;  // dynamic shared memory
     int32_t N, T;
     int32_t iter0;       // plain path: the iteration this launch performs
     int32_t first_iter;  // n of the first iteration
     int32_t last_iter;   // n of the last iteration
     int32_t update_last; // update after the last iteration too
-    uint32_t stream_id;
-    float eps0, dR, Rmin, Rmax, max_step;
+    uint32_t rk0[10];    // Philox round keys: key + r * Weyl constant
+    uint32_t rk1[10];
+    float dR, Rmin, Rmax;
+    float half_eps0;     // eps0 / 2: eta_n = half_eps0 / sqrt(n)
+    float max_step, max_step2;
+    float rho, inv_dr, inv_dR;   // weight bands (dr = rho dR)
+    float kR1, kR2;      // dS/dR on the inner / outer band
+    float kr1, kr2;      // -dS/dr on the inner / outer band
+    float vol_coef;      // (4/3 pi or pi) / N: ball measure per sample, over Ro^d
     float *trace;        // optional (volume 0 only)
     int64_t tk0, tk1;
     int32_t tt0, tt1;
     int32_t *status;
+    unsigned long long *path_counts;   // [3]: fast, clamped, global contour-iterations
 };
 
 // ----------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC'11): 10 rounds of the 4x32 bijection with
-// multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key increments 0x9E3779B9 /
-// 0xBB67AE85.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+// multipliers 0xD2511F53 / 0xCD9E8D57; the round keys (key plus r times the Weyl
+// constants 0x9E3779B9 / 0xBB67AE85) are launch constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, const uint32_t *rk1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
+    }
+    return c;
+}
+
+// Same generator with the key schedule computed in registers (test entry point).
+__device__ __forceinline__ uint4 philox4x32_10_key(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -80,16 +103,85 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// top 24 bits of a word as a uniform in [0, 1) (exact in FP32)
-__device__ __forceinline__ float u24(uint32_t w)
+// top 24 bits of a word as an exact float in [0, 2^24)
+__device__ __forceinline__ float top24(uint32_t w) { return __uint2float_rn(w >> 8); }
+
+// ----------------------------------------------------------------- fast functions
+// Hardware approximations (MUFU): their errors (sqrt, lg2/ex2 ~2^-22 relative,
+// sin/cos ~2^-20.5 absolute on [-pi, pi]) move a sample by well under 1e-5 voxel.
+__device__ __forceinline__ float sqrt_approx(float x)
 {
-    return __uint2float_rn(w >> 8) * 5.9604644775390625e-8f;
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// x + y rounded toward minus infinity
+__device__ __forceinline__ float add_rd(float x, float y) { return __fadd_rd(x, y); }
+
+// Accurate (about 1 ulp) cosine and sine of the azimuth 2 pi m / 2^24 of a 24-bit
+// integer m, both negated (the raw-direction convention of the kernels): m is split
+// exactly into a quarter-turn index q and a remainder y in [-1/2, 1/2) quarter
+// turns; sin(pi y/2) = y P(y^2), cos(pi y/2) = Q(y^2) with the fitted polynomials of
+// gen_sincos_coeffs.py; the quarter turns rotate and flip the pair.
+__device__ __forceinline__ void neg_sincos_turn(uint32_t m, float &nc, float &ns)
+{
+    const uint32_t q = (m + (1u << 21)) >> 22;                  // nearest quarter turn, 0..4
+    const uint32_t f = m + (1u << 22) - (q << 22);              // remainder + 2^22, in [2^21, 3 2^21)
+    // (2^23 + f) - (2^23 + 2^22) is exact: f stays inside the 23-bit mantissa
+    const float y = (__uint_as_float(0x4B000000u + f) - 12582912.0f) * 2.384185791015625e-7f;
+    const float y2 = y * y;
+    const float s = y * fmaf(fmaf(fmaf(-0.004602177068591118f, y2, 0.07968022674322128f), y2,
+                                  -0.6459634900093079f), y2, 1.5707963705062866f);
+    const float c = fmaf(fmaf(fmaf(fmaf(0.0009036316769197583f, y2, -0.02086007222533226f), y2,
+                                   0.25366920232772827f), y2, -1.2337005138397217f), y2, 1.0f);
+    const bool odd = (q & 1u) != 0;
+    const float cc = odd ? s : c, ss = odd ? c : s;
+    nc = __int_as_float(__float_as_int(cc) ^ (int)(((q + 3u) & 2u) << 30));   // -cos: flip for q in {0, 3}
+    ns = __int_as_float(__float_as_int(ss) ^ (int)((((q & 2u) ^ 2u)) << 30)); // -sin: flip for q in {0, 1}
 }
 
-// ----------------------------------------------------------------- voxel loads
+// ----------------------------------------------------------------- voxel values
+// Exact conversion of a stored voxel to float.  Integers below 2^23 go through the
+// bit pattern of 2^23 + v (two integer/FMA-pipe instructions, no conversion unit).
 template <typename T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<uint8_t>(uint8_t v) { return (float)v; }
-template <> __device__ __forceinline__ float to_f<uint16_t>(uint16_t v) { return (float)v; }
+template <> __device__ __forceinline__ float to_f<uint8_t>(uint8_t v)
+{
+    return __uint_as_float(0x4B000000u | (uint32_t)v) - 8388608.0f;
+}
+template <> __device__ __forceinline__ float to_f<uint16_t>(uint16_t v)
+{
+    return __uint_as_float(0x4B000000u | (uint32_t)v) - 8388608.0f;
+}
 template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
 
@@ -163,39 +255,12 @@ __device__ __forceinline__ AxisSplit split_axis(float c, float sp, float inv_sp,
 // Clamp-to-edge multilinear interpolation along one axis: the base tap (relative
 // to the centre voxel) and the fraction.  Clamping the coordinate to [0, n-1] and
 // the base tap to n-2 gives exactly the interpolant with clamped tap indices.
-__device__ __forceinline__ void axis_tap(const AxisSplit &a, float off, int &base, float &fr)
+__device__ __forceinline__ void axis_tap(const AxisSplit &a, float x, int &base, float &fr)
 {
-    float x = a.cf + off;
     x = fminf(fmaxf(x, a.lo), a.hi);
     const float fl = fminf(floorf(x), a.top);
     fr = x - fl;
     base = (int)fl;
-}
-
-// ----------------------------------------------------------------- weight function
-// S(r;R) = -1 + 2 ramp((r - rho R)/dr) - ramp((r - R)/dR), ramp(t) = clamp(t+1/2, 0, 1),
-// dr = dR / 2^(1/d) (Eq. 5 and the relation below it); band membership t in [-1/2, 1/2).
-struct WeightConsts {
-    float a1, b1;  // t1 + 1/2 = r a1 + b1
-    float a2, b2;  // t2 + 1/2 = r a2 + b2
-    float kR1, kR2; // dS/dR on the inner / outer band
-    float kr1, kr2; // -dS/dr on the inner / outer band
-};
-
-__device__ __forceinline__ WeightConsts weight_consts(float R, float dR, int ndim)
-{
-    const float rho = ndim == 3 ? 0.79370052598409973738f : 0.70710678118654752440f;
-    const float dr = dR * rho;
-    WeightConsts w;
-    w.a1 = 1.0f / dr;
-    w.b1 = 0.5f - rho * R / dr;
-    w.a2 = 1.0f / dR;
-    w.b2 = 0.5f - R / dR;
-    w.kR1 = -2.0f * rho / dr;
-    w.kR2 = 1.0f / dR;
-    w.kr1 = -2.0f / dr;
-    w.kr2 = 1.0f / dR;
-    return w;
 }
 
 }  // namespace ac

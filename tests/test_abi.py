@@ -69,7 +69,7 @@ def test_struct_layouts_match_header(ac, tmp_path):
     checks = {
         "ac_evolve_params": ["N", "T", "eps0", "dR", "Rmin", "Rmax", "max_step", "seed", "stream_id", "path",
                              "lanes_per_contour", "compensated", "brick", "warps_per_block", "first_iter",
-                             "update_last"],
+                             "update_last", "sampling"],
         "ac_trace": ["device_buf", "k_begin", "k_end", "t_begin", "t_end"],
         "ac_cell": ["c", "r", "E", "id"],
         "ac_seed_params": ["stride", "R0"],

@@ -161,11 +161,12 @@ def crop2d():
     return synth.large_2d(1, shape=(512, 512), n_nuclei=188)
 
 
-@pytest.mark.parametrize("path,G", [(0, 32), (0, 16), (1, 32)])
-def test_teacher_forced_2d(ac, oracle, crop2d, path, G):
+@pytest.mark.parametrize("path,G,N,sampling", [(0, 32, 128, 0), (0, 16, 128, 0), (0, 8, 128, 0), (1, 32, 128, 0),
+                                              (0, 8, 128, 1), (0, 8, 3, 0), (1, 8, 1, 0)])
+def test_teacher_forced_2d(ac, oracle, crop2d, path, G, N, sampling):
     s = crop2d
     R0 = 6.0 / math.sqrt(1.5)
-    p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=99, path=path, lanes_per_contour=G)
+    p = ac.default_params(2, R0, s.contrast, N=N, T=100, seed=99, path=path, lanes_per_contour=G, sampling=sampling)
     r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(1000, 2500))
     img = P.oracle_image(oracle, s.volume, s.spacing)
     frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 1000, 1)
@@ -209,10 +210,13 @@ def test_teacher_forced_storage_types(ac, oracle, brain_small, kind):
 
 
 # ------------------------------------------------------------------ edge cases
-@pytest.mark.parametrize("N,T,G", [(1, 3, 32), (33, 4, 32), (100, 5, 16), (7, 2, 8)])
-def test_ragged_sample_counts(ac, oracle, small3d, N, T, G):
+@pytest.mark.parametrize("N,T,G,sampling", [(1, 3, 32, 0), (2, 3, 8, 0), (33, 4, 32, 0), (100, 5, 16, 0),
+                                            (7, 2, 8, 0), (256, 3, 16, 1), (100, 3, 32, 2)])
+def test_ragged_sample_counts(ac, oracle, small3d, N, T, G, sampling):
+    """Sample counts that leave lanes idle or ragged; N < 64 selects the accurate
+    sample arithmetic automatically (per-sample errors are not averaged away)."""
     s = small3d
-    p = _p3(ac, s, N=N, T=T, lanes_per_contour=G)
+    p = _p3(ac, s, N=N, T=T, lanes_per_contour=G, sampling=sampling)
     r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0, trace_k=(100, 700))
     img = P.oracle_image(oracle, s.volume, s.spacing)
     frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], 100, 1)
@@ -238,25 +242,42 @@ def test_tiny_volumes_and_out_of_volume_balls(ac, oracle, ndim):
 
 
 def test_global_fallback_when_contours_outgrow_the_halo(ac, oracle):
-    """Seeds with a tiny radius give a small halo; on a big blob they grow out of
-    the staged region and read the global volume -- same results either way."""
+    """Seeds with a radius of 1 size the halo (about 5 voxels); their radius is then
+    set to 7 with ac_set_state, so the balls leave the staged region and read the
+    global volume -- same results as the oracle and as the plain path."""
     from paper_1804_06304_gb300 import synth
-    vol = synth.sphere_volume((48, 48, 48), (23.7, 24.2, 23.9), 9.0)
+    vol = synth.sphere_volume((48, 48, 48), (23.7, 24.2, 23.9), 9.0, noise=5.0, seed=2)
     seeds = np.array([[23 + dx, 24 + dy, 24, 1.0] for dx in (-2, 0, 2) for dy in (-2, 0, 2)], np.float32)
-    p = ac.EvolveParams(N=256, T=30, eps0=8.0 / 170.0, dR=1.0, Rmin=0.5, Rmax=20.0, seed=3)
-    r = P.gpu_run(ac, vol, (1, 1, 1), p, explicit=seeds, trace_k=(0, 9))
-    assert r["final"][3].max() > 6.0          # grew well past the halo of ~5 voxels
-    img = P.oracle_image(oracle, vol, (1, 1, 1))
-    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], 0, 1)
-    assert frac == 1.0, (worst, bad)
-    p2 = ac.EvolveParams(**{**p.__dict__, "path": 1})
-    r2 = P.gpu_run(ac, vol, (1, 1, 1), p2, explicit=seeds)
-    np.testing.assert_array_equal(r["final"], r2["final"])
+    p = ac.EvolveParams(N=256, T=12, eps0=8.0 / 170.0, dR=1.0, Rmin=0.5, Rmax=20.0, seed=3)
+    outs = []
+    for path in (0, 1):
+        V = ac.ac_create_volume(vol)
+        C = ac.ac_seed(V, explicit=seeds)
+        st = ac.ac_get_state(C)
+        st[3] = 7.0
+        ac.ac_set_state(C, st)
+        import torch
+        buf = torch.zeros(12 * 9 * 9, device="cuda")
+        ac.ac_evolve(C, ac.EvolveParams(**{**p.__dict__, "path": path}), trace=(buf, 0, 9, 1, 13))
+        fast, clamped, glob = ac.ac_evolve_stats(C)
+        assert fast + clamped + glob == 9 * 12
+        if path == 0:
+            assert glob >= 9 * 6, (fast, clamped, glob)
+            tr = buf.view(12, 9, 9).cpu().numpy()
+            img = P.oracle_image(oracle, vol, (1, 1, 1))
+            frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), tr, 0, 1)
+            assert frac == 1.0, (worst, bad)
+        else:
+            assert glob == 9 * 12
+        outs.append(ac.ac_get_state(C))
+    np.testing.assert_array_equal(outs[0], outs[1])
 
 
 def test_brick_and_plain_paths_agree_bitwise(ac, small3d):
     s = small3d
     a = P.gpu_run(ac, s.volume, s.spacing, _p3(ac, s, T=20), stride=4.0)
+    fast, clamped, glob = ac.ac_evolve_stats(a["ctr"])
+    assert fast + clamped + glob == 2048 * 20 and fast > 0 and clamped > 0
     b = P.gpu_run(ac, s.volume, s.spacing, _p3(ac, s, T=20, path=1), stride=4.0)
     np.testing.assert_array_equal(a["final"], b["final"])
 
@@ -280,12 +301,12 @@ def test_batch_equals_single(ac):
     p = ac.default_params(3, 4.0 / math.sqrt(1.5), 170.0, N=128, T=15)
     singles, sets, keep = [], [], []
     for i, s in enumerate(vols):
-        r = P.gpu_run(ac, s.volume, s.spacing, ac.EvolveParams(**{**p.__dict__, "seed": 100 + i}), stride=4.0)
+        r = P.gpu_run(ac, s.volume, s.spacing, ac.EvolveParams(**{**p.__dict__, "stream_id": 100 + i}), stride=4.0)
         singles.append(r["final"])
         V = ac.ac_create_volume(s.volume)
         keep.append(V)
         sets.append(ac.ac_seed(V, stride=4.0))
-    ac.ac_evolve_batch(sets, p, seeds=[100 + i for i in range(len(vols))])
+    ac.ac_evolve_batch(sets, p, stream_ids=[100 + i for i in range(len(vols))])
     for c, want in zip(sets, singles):
         np.testing.assert_array_equal(ac.ac_get_state(c), want)
 
