@@ -36,11 +36,16 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-# Algorithmic ALU work per sample, in issue slots (a warp instruction issued for
-# 32 lanes counts 32): Philox4x32-10, uniform conversion, ball/disk map, tap
-# setup, gather and interpolation, weight bands, compensated accumulation.  The
-# derivation is tabulated in the design notes.
-ALG_SLOTS_PER_SAMPLE = {2: 115.0, 3: 177.0}
+# Algorithmic ALU work per sample, in lane issue slots: the lean operation count of
+# one sample -- Philox4x32-10 (10 rounds of two wide multiplies and two three-input
+# XORs per block), word-to-float conversions, radius and direction (hardware
+# sqrt / lg2+ex2 / sin / cos), index offsets, floor and fraction per axis, the
+# gather and multilinear interpolation, the two weight bands, and compensated
+# accumulation of the four (2D) or five (3D) sums.  2D: 76 (a Philox block serves
+# two samples; one 128-bit load per bilinear gather); 3D: 147 (one block per
+# sample; eight 8/16-bit taps with exact integer-to-float conversion).  The
+# per-iteration reduction and update are excluded.  Tabulated in the design notes.
+ALG_SLOTS_PER_SAMPLE = {2: 76.0, 3: 147.0}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0
