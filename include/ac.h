@@ -180,6 +180,42 @@ ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_t
 ac_status ac_evolve_batch(ac_contours *const *sets, const uint32_t *stream_ids, int32_t n_sets,
                           const ac_evolve_params *params, void *cuda_stream);
 
+/*
+ * ac_evolve_static -- ac_evolve for callers that cannot allocate device memory.
+ * Some callers must not call cudaMalloc: code whose device memory is owned by
+ * its own allocator (a framework's caching allocator that has reserved the free
+ * memory, or a pool sized once at start-up), and latency-critical loops where an
+ * allocation could block or synchronize the device.  This entry point makes no
+ * allocation: the caller passes the volume and the contour state in device memory
+ * it owns, and every temporary (binning keys, sort space, volume descriptor,
+ * TMA descriptor, status word) lives in one file-scope device array of
+ * AC_STATIC_SCRATCH_BYTES that every GPU using the library holds until the
+ * process exits.  The paper has no counterpart: it describes no memory
+ * management.
+ *   volume_dev   voxels on the current device, element strides (1, row_stride,
+ *                plane_stride) (0 = dense); the brick path needs a 16-byte
+ *                aligned base and row/plane strides that are multiples of 16
+ *                bytes (AC_PATH_PLAIN takes any layout)
+ *   state_dev    5 x n_contours float32 (cx[], cy[], cz[], R[], E[]), updated in
+ *                place; 1 <= n_contours <= AC_STATIC_MAX_CONTOURS
+ *   r0, stride   radius and lattice spacing the contours were seeded with (they
+ *                size the bricks), > 0
+ * Other arguments and the iteration semantics are those of ac_create_volume and
+ * ac_evolve.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (several
+ * streams or threads) race and must be serialised by the caller.  Synchronizes
+ * the stream and reports the status word.  Errors: AC_ERR_BUDGET (n_contours or
+ * the sort space beyond the array), AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_TIMEOUT,
+ * AC_ERR_NUMERIC.
+ */
+#define AC_STATIC_MAX_CONTOURS (1 << 20)
+#define AC_STATIC_SCRATCH_BYTES (32u << 20)
+ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, int ndim, const int64_t dims[3],
+                           int64_t row_stride, int64_t plane_stride, const float spacing[3],
+                           float intensity_scale, float *state_dev, int64_t n_contours, float r0,
+                           float stride, const ac_evolve_params *params, void *cuda_stream);
+
 /* ------------------------------------------------------------------ localize -- */
 /*
  * ac_localize -- energy cull and overlap competition (stage a9, section "Results

@@ -80,6 +80,9 @@ _SIGS = {
     "ac_evolve_kernel_ms": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_float)]),
     "ac_kernel_launches": (ct.c_int64, []),
     "ac_evolve_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p]),
+    "ac_evolve_static": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
+                                    ct.POINTER(ct.c_float), ct.c_float, ct.c_void_p, ct.c_int64, ct.c_float,
+                                    ct.c_float, ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_last_error": (ct.c_char_p, []),
 }
 
@@ -362,6 +365,29 @@ def ac_evolve_stats(ctr: Contours, stream=None) -> tuple:
 
 def ac_kernel_launches() -> int:
     return int(load().ac_kernel_launches())
+
+
+AC_STATIC_MAX_CONTOURS = 1 << 20
+
+
+def ac_evolve_static(volume_dev, state_dev, params: EvolveParams, r0: float, stride: float,
+                     spacing=(1.0, 1.0, 1.0), intensity_scale: float = 1.0, dtype: int | None = None,
+                     n_contours: int | None = None, stream=None):
+    """Allocation-free evolve for callers that own all device memory: ``volume_dev``
+    (CUDA tensor, [z, y, x] or [y, x]) and ``state_dev`` (CUDA float32 tensor of
+    shape (5, C), updated in place) belong to the caller; the library's temporaries
+    live in its fixed device array.  Synchronizes the stream."""
+    ptr, on_dev, code, shape, strides = _ptr(volume_dev)
+    if dtype is not None:
+        code = dtype
+    ndim = len(shape)
+    dims = (ct.c_int64 * 3)(*(list(shape[::-1]) + [1] * (3 - ndim)))
+    sp = (ct.c_float * 3)(*[float(v) for v in (list(spacing) + [1.0] * 3)[:3]])
+    C = int(state_dev.shape[1]) if n_contours is None else int(n_contours)
+    p = params.to_c()
+    _check(load().ac_evolve_static(ct.c_void_p(ptr), code, ndim, dims, strides[-2], strides[-3] if ndim == 3 else 0,
+                                   sp, intensity_scale, ct.c_void_p(state_dev.data_ptr()), C, float(r0), float(stride),
+                                   ct.byref(p), ct.c_void_p(_stream(stream))))
 
 
 def ac_last_error() -> str:

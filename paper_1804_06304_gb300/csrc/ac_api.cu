@@ -756,6 +756,221 @@ ac_status evolve_sets(ac_contours *const *sets, const uint32_t *streams, int n_s
 
 }  // namespace
 
+// ------------------------------------------------------------------ allocation-free evolve
+// One file-scope device array holds every temporary of ac_evolve_static.  Byte
+// layout: [0, 16) status word, [64, 96) path counters, [256, ...) volume
+// descriptor, [512, 640) TMA descriptor, [1024, ...) binning keys, contour indices
+// and their sorted copies (4 x 4 bytes per contour), then the sort's temporary
+// space up to the end of the array.
+static __device__ __align__(256) unsigned char g_static_scratch[AC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr size_t kStaticDesc = 256, kStaticTmap = 512, kStaticArrays = 1024;
+static_assert(sizeof(VolDesc) <= kStaticTmap - kStaticDesc, "descriptor slot too small");
+
+// Device address of the array on `dev`, looked up once per device.  In host code
+// the array's name is only a host-side stand-in, never a device address.
+ac_status static_scratch_ptr(int dev, unsigned char **out)
+{
+    static std::mutex mu;
+    static void *addr[128] = {nullptr};
+    if (dev < 0 || dev >= 128) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(addr[dev]);
+    return AC_OK;
+}
+
+}  // namespace
+
+extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, int ndim, const int64_t dims[3],
+                                      int64_t row_stride, int64_t plane_stride, const float spacing[3],
+                                      float intensity_scale, float *state_dev, int64_t n_contours, float r0,
+                                      float stride, const ac_evolve_params *p, void *cuda_stream)
+{
+    g_err.clear();
+    if (n_contours > AC_STATIC_MAX_CONTOURS)
+        AC_FAIL(AC_ERR_BUDGET, "ac_evolve_static: n_contours exceeds AC_STATIC_MAX_CONTOURS (" +
+                                   std::to_string(AC_STATIC_MAX_CONTOURS) + ")");
+    if (n_contours < 1) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: need at least one contour");
+    if (!volume_dev || !state_dev || !dims || !spacing) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: NULL argument");
+    ac_status s = check_params(p);
+    if (s != AC_OK) return s;
+    const int es = elem_size(dtype);
+    if (es == 0) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: unknown dtype");
+    if (ndim != 2 && ndim != 3) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: ndim must be 2 or 3");
+    ac_volume vol;
+    vol.dtype = dtype;
+    vol.ndim = ndim;
+    vol.es = es;
+    vol.scale = intensity_scale;
+    for (int d = 0; d < 3; ++d) {
+        vol.n[d] = d < ndim ? dims[d] : 1;
+        vol.sp[d] = d < ndim ? spacing[d] : 1.0f;
+        if (d < ndim && (vol.n[d] < 2 || vol.n[d] > (1 << 30) || !(vol.sp[d] > 0.0f) || !std::isfinite(vol.sp[d])))
+            AC_FAIL(AC_ERR_ARG, "ac_evolve_static: every used dimension must be in [2, 2^30] with positive spacing");
+    }
+    if (row_stride == 0) row_stride = vol.n[0];
+    if (plane_stride == 0) plane_stride = row_stride * vol.n[1];
+    if (row_stride < vol.n[0] || plane_stride < row_stride * vol.n[1])
+        AC_FAIL(AC_ERR_ARG, "ac_evolve_static: strides smaller than the extents");
+    if (!std::isfinite(intensity_scale)) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: intensity_scale not finite");
+    vol.data = const_cast<void *>(volume_dev);
+    vol.pitch_y = row_stride;
+    vol.pitch_z = plane_stride;
+    vol.bytes = (size_t)plane_stride * vol.n[2] * es;
+    const bool brick = p->path == AC_PATH_BRICK;
+    if (brick && (((uintptr_t)volume_dev % 16) != 0 || (row_stride * es) % 16 != 0 || (plane_stride * es) % 16 != 0))
+        AC_FAIL(AC_ERR_ARG, "ac_evolve_static: the brick path needs a 16-byte aligned volume with row and plane "
+                            "strides that are multiples of 16 bytes (use AC_PATH_PLAIN otherwise)");
+    if (brick && (!(r0 > 0.0f) || !(stride > 0.0f)))
+        AC_FAIL(AC_ERR_ARG, "ac_evolve_static: r0 and stride must be positive");
+    cudaPointerAttributes pa;
+    for (const void *q : {volume_dev, (const void *)state_dev}) {
+        if (cudaPointerGetAttributes(&pa, q) != cudaSuccess ||
+            (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            AC_FAIL(AC_ERR_ARG, "ac_evolve_static: volume and state must be device memory");
+        }
+    }
+    int dev = 0;
+    AC_CUDA(cudaGetDevice(&dev));
+    unsigned char *base = nullptr;
+    s = static_scratch_ptr(dev, &base);
+    if (s != AC_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    ac_contours ctr;   // host-side view of the caller's state (nothing allocated)
+    ctr.vol = &vol;
+    ctr.C = n_contours;
+    ctr.state = state_dev;
+    ctr.status = reinterpret_cast<int32_t *>(base);
+    ctr.path_counts = reinterpret_cast<unsigned long long *>(base + 64);
+    ctr.r_hint = r0;
+    ctr.stride_hint = stride;
+    Plan pl;
+    s = plan_evolve(&vol, stride, r0, p, pl);
+    if (s != AC_OK) return s;
+
+    EvolveArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_vols = 1;
+    a.ndim = ndim;
+    a.total_contours = n_contours;
+    a.N = p->N;
+    a.T = p->T;
+    a.first_iter = p->first_iter ? p->first_iter : 1;
+    a.last_iter = a.first_iter + p->T - 1;
+    a.update_last = p->update_last ? 1 : 0;
+    {
+        uint32_t k0 = (uint32_t)p->seed, k1 = (uint32_t)(p->seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            a.rk0[r] = k0;
+            a.rk1[r] = k1;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const double rho = std::pow(2.0, -1.0 / ndim), dR = p->dR, dr = rho * dR;
+        a.dR = p->dR;
+        a.Rmin = p->Rmin;
+        a.Rmax = p->Rmax;
+        a.half_eps0 = (float)(0.5 * p->eps0);
+        a.max_step = p->max_step;
+        a.max_step2 = (float)((double)p->max_step * p->max_step);
+        a.rho = (float)rho;
+        a.inv_dr = (float)(1.0 / dr);
+        a.inv_dR = (float)(1.0 / dR);
+        a.kR1 = (float)(-2.0 * rho / dr);
+        a.kR2 = (float)(1.0 / dR);
+        a.kr1 = (float)(-2.0 / dr);
+        a.kr2 = (float)(1.0 / dR);
+        a.vol_coef = (float)((ndim == 3 ? 4.0 / 3.0 * M_PI : M_PI) / p->N);
+    }
+    a.status = ctr.status;
+    a.path_counts = ctr.path_counts;
+
+    VolDesc desc = make_desc(&ctr, p->stream_id);
+    int64_t bricks = 1;
+    if (brick)
+        for (int d = 0; d < 3; ++d) {
+            desc.nb[d] = (int32_t)((vol.n[d] + pl.B[d] - 1) / pl.B[d]);
+            bricks *= desc.nb[d];
+        }
+    VolDesc *ddesc = reinterpret_cast<VolDesc *>(base + kStaticDesc);
+    a.vols = ddesc;
+    // start from a clean status word and counters every call (the array keeps the last call's contents)
+    AC_CUDA(cudaMemsetAsync(base, 0, 96, st));
+    AC_CUDA(cudaMemcpyAsync(ddesc, &desc, sizeof(desc), cudaMemcpyHostToDevice, st));
+
+    if (!brick) {
+        const int64_t per_cta = (int64_t)pl.warps * 32 / pl.G;
+        const int64_t grid = std::min<int64_t>((n_contours + per_cta - 1) / per_cta, (int64_t)1 << 30);
+        for (int n = a.first_iter; n <= a.last_iter; ++n) {
+            a.iter0 = n;
+            cudaError_t e = launch_evolve(dtype, a, pl, grid, st);
+            if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve_static: launch: ") + cudaGetErrorString(e));
+            count_launch();
+        }
+    } else {
+        if (bricks >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: too many bricks");
+        PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+        if (!enc) AC_FAIL(AC_ERR_CUDA, "ac_evolve_static: cuTensorMapEncodeTiled is not available from the driver");
+        CUtensorMap map;
+        cuuint64_t gdim[3] = {(cuuint64_t)vol.n[0], (cuuint64_t)vol.n[1], (cuuint64_t)vol.n[2]};
+        cuuint64_t gstride[2] = {(cuuint64_t)(row_stride * es), (cuuint64_t)(plane_stride * es)};
+        cuuint32_t box[3] = {(cuuint32_t)pl.ext[0], (cuuint32_t)pl.ext[1], (cuuint32_t)pl.ext[2]};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&map, tma_type(dtype), 3, vol.data, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            AC_FAIL(AC_ERR_CUDA, "ac_evolve_static: cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+        CUtensorMap *dmap = reinterpret_cast<CUtensorMap *>(base + kStaticTmap);
+        AC_CUDA(cudaMemcpyAsync(dmap, &map, sizeof(map), cudaMemcpyHostToDevice, st));
+        uint32_t *keys = reinterpret_cast<uint32_t *>(base + kStaticArrays);
+        uint32_t *vals = keys + AC_STATIC_MAX_CONTOURS;
+        uint32_t *skeys = vals + AC_STATIC_MAX_CONTOURS;
+        uint32_t *svals = skeys + AC_STATIC_MAX_CONTOURS;
+        unsigned char *tmp_space = reinterpret_cast<unsigned char *>(svals + AC_STATIC_MAX_CONTOURS);
+        const size_t tmp_cap = (size_t)AC_STATIC_SCRATCH_BYTES - (size_t)(tmp_space - base);
+        int end_bit = 1;
+        while (((int64_t)1 << end_bit) < bricks + 1) ++end_bit;
+        size_t tmp = 0;
+        AC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, keys, skeys, vals, svals, (int)n_contours, 0, end_bit, st));
+        if (tmp > tmp_cap)
+            AC_FAIL(AC_ERR_BUDGET, "ac_evolve_static: the sort needs " + std::to_string(tmp) +
+                                       " bytes of temporary space, more than the static array holds");
+        const int64_t blocks = std::min<int64_t>((n_contours + 255) / 256, 1 << 16);
+        bin_kernel<<<(unsigned)blocks, 256, 0, st>>>(ddesc, 1, n_contours, make_int3(pl.B[0], pl.B[1], pl.B[2]), keys,
+                                                     vals);
+        count_launch();
+        AC_CUDA(cudaGetLastError());
+        AC_CUDA(cub::DeviceRadixSort::SortPairs(tmp_space, tmp, keys, skeys, vals, svals, (int)n_contours, 0, end_bit, st));
+        a.tmaps = dmap;
+        a.sorted_brick = skeys;
+        a.sorted_gidx = svals;
+        a.total_bricks = bricks;
+        for (int d = 0; d < 3; ++d) {
+            a.B[d] = pl.B[d];
+            a.halo[d] = pl.halo[d];
+            a.ext[d] = pl.ext[d];
+        }
+        a.raw_bytes = pl.raw;
+        a.quad_off = pl.quad_off;
+        a.smem_bytes = pl.smem;
+        cudaError_t e = launch_evolve(dtype, a, pl, bricks, st);
+        if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve_static: launch: ") + cudaGetErrorString(e));
+        count_launch();
+    }
+    return check_status(&ctr, st);
+}
+
 extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_trace *trace,
                                void *cuda_stream)
 {
