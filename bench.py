@@ -166,6 +166,28 @@ def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0):
     return samples / dt, threads, f"{m} of {len(seeds)} contours (random, seed {rng_seed}), all {wl['T']} iterations"
 
 
+# ------------------------------------------------------------------------ ranks
+def aggregate_ranks(local_ms: list, samples_per_rank: int, world: int, reduce_max=None) -> tuple:
+    """Whole-job throughput of independent replicas: each rank's mean step time,
+    the maximum over ranks (``reduce_max`` all-reduces a float with MAX; None on a
+    single rank), and value = world x samples per rank / that time."""
+    t = float(np.mean(local_ms))
+    if reduce_max is not None:
+        t = reduce_max(t)
+    return t, world * samples_per_rank / (t * 1e-3)
+
+
+def torch_max_reducer(device):
+    import torch
+    import torch.distributed as dist
+
+    def f(x: float) -> float:
+        v = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        return float(v[0])
+    return f
+
+
 # ------------------------------------------------------------------------ main
 def main(argv=None):
     ap = argparse.ArgumentParser()
@@ -180,6 +202,7 @@ def main(argv=None):
     ap.add_argument("--compensated", type=int, default=1)
     ap.add_argument("--brick", type=str, default="0,0,0")
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--halo", type=float, default=0.0, help="halo factor (0 = library default)")
     ap.add_argument("--size", type=int, default=0, help="image side (smaller instances for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,7 +244,8 @@ def main(argv=None):
     params = ac.default_params(ndim, R0, s.contrast, N=wl["N"], T=wl["T"], seed=1000 + rank,
                                path=ac.AC_PATH_BRICK if args.path == "brick" else ac.AC_PATH_PLAIN,
                                lanes_per_contour=args.lanes, compensated=args.compensated,
-                               brick=tuple(int(x) for x in args.brick.split(",")), warps_per_block=args.warps)
+                               brick=tuple(int(x) for x in args.brick.split(",")), warps_per_block=args.warps,
+                               halo_factor=args.halo)
     E0 = ac.default_E0(ndim, s.contrast)
 
     def step(src):
@@ -259,20 +283,16 @@ def main(argv=None):
         n_cells = len(cells)
     torch.cuda.synchronize()
     launches = ac.ac_kernel_launches() - launches0
+    paths = ac.ac_evolve_stats(C)
     if dist_on:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_ms = float(np.mean(step_ms))
-    k_ms = float(np.mean(kernel_ms))
-    if dist_on:
-        t = torch.tensor([t_ms, k_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms, k_ms = float(t[0]), float(t[1])
-
     samples = C.count * wl["N"] * wl["T"]
-    value = world * samples / (t_ms * 1e-3)
+    reducer = torch_max_reducer(dev) if dist_on else None
+    t_ms, value = aggregate_ranks(step_ms, samples, world, reducer)
+    k_ms, _ = aggregate_ranks(kernel_ms, samples, world, reducer)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -287,12 +307,8 @@ def main(argv=None):
             b1.record()
             b1.synchronize()
             e2e_ms.append(b0.elapsed_time(b1))
-        e_ms = float(np.mean(e2e_ms))
-        if dist_on:
-            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t[0])
-        e2e = {"value": world * samples / (e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e_ms,
+        e_ms, e_val = aggregate_ranks(e2e_ms, samples, world, reducer)
+        e2e = {"value": e_val, "unit": "samples/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(len(cells) * 24 + 4 * 6)}
 
     achieved = ALG_SLOTS_PER_SAMPLE[ndim] * samples / (k_ms * 1e-3) / 1e12
@@ -320,6 +336,7 @@ def main(argv=None):
             "voxels_per_s": world * int(np.prod(vol.shape)) / (t_ms * 1e-3),
             "evolve_samples_per_s": world * samples / (k_ms * 1e-3),
             "cells": n_cells,
+            "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
             "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         }

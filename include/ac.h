@@ -145,7 +145,8 @@ typedef struct {
     uint64_t seed;             /* Philox key                                          */
     uint32_t stream_id;        /* fourth Philox counter word                          */
     int32_t path;              /* ac_path                                             */
-    int32_t lanes_per_contour; /* 8, 16 or 32 lanes cooperate on one contour; 0=auto  */
+    int32_t lanes_per_contour; /* 4, 8, 16 or 32 lanes cooperate on one contour; 0 =
+                                  auto (4 needs compensated sums, fast sampling)      */
     int32_t compensated;       /* 1: compensated (Kahan + TwoSum) sums, 0: plain FP32 */
     int32_t brick[3];          /* brick interior in voxels per axis; 0 = auto          */
     int32_t warps_per_block;   /* 0 = auto                                            */
@@ -157,6 +158,9 @@ typedef struct {
                                   1 accurate (correctly rounded sqrt/cbrt, ~1 ulp
                                   sine/cosine), 2 fast (hardware approximations,
                                   ~2^-20 absolute direction error)                    */
+    float halo_factor;         /* brick halo = halo_factor x the largest initial radius
+                                  + dR/2 + 2 voxels (0 = auto); balls that outgrow it
+                                  read the global volume for that iteration           */
 } ac_evolve_params;
 
 typedef struct {
@@ -171,13 +175,23 @@ ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_t
 
 /*
  * ac_evolve_batch -- one launch over several contour sets, each on its own volume
- * (the batching form: uneven volumes and contour counts in one persistent pass).
- * params are shared, including the Philox key (params->seed); set i draws its
- * samples with the fourth counter word stream_ids[i] (NULL: params->stream_id for
- * every set), so set i gives exactly what ac_evolve on that set alone gives with
- * stream_id = stream_ids[i].  Asynchronous.  Errors as ac_evolve.
+ * (the batching form: uneven volumes and contour counts in one pass over all
+ * iterations).  params are shared, including the Philox key (params->seed); set i
+ * runs iterations items[i].first_iter .. first_iter + n_iter - 1 (update after the
+ * last one if items[i].update_last) with fourth counter word items[i].stream_id,
+ * so it gives exactly what ac_evolve on that set alone gives with those values.
+ * items NULL: every set uses params' stream_id, first_iter, T and update_last.
+ * A set with n_iter = 0 is left untouched.  Every set must share dtype and ndim.
+ * Asynchronous.  Errors as ac_evolve.
  */
-ac_status ac_evolve_batch(ac_contours *const *sets, const uint32_t *stream_ids, int32_t n_sets,
+typedef struct {
+    uint32_t stream_id;   /* fourth Philox counter word of the set             */
+    int32_t first_iter;   /* first iteration n (>= 1)                          */
+    int32_t n_iter;       /* iterations this call (>= 0)                       */
+    int32_t update_last;  /* 1: update after the last one too                  */
+} ac_batch_item;
+
+ac_status ac_evolve_batch(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
                           const ac_evolve_params *params, void *cuda_stream);
 
 /*

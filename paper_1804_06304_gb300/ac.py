@@ -39,12 +39,18 @@ class ac_evolve_params(ct.Structure):
                 ("Rmin", ct.c_float), ("Rmax", ct.c_float), ("max_step", ct.c_float), ("seed", ct.c_uint64),
                 ("stream_id", ct.c_uint32), ("path", ct.c_int32), ("lanes_per_contour", ct.c_int32),
                 ("compensated", ct.c_int32), ("brick", ct.c_int32 * 3), ("warps_per_block", ct.c_int32),
-                ("first_iter", ct.c_int32), ("update_last", ct.c_int32), ("sampling", ct.c_int32)]
+                ("first_iter", ct.c_int32), ("update_last", ct.c_int32), ("sampling", ct.c_int32),
+                ("halo_factor", ct.c_float)]
 
 
 class ac_trace(ct.Structure):
     _fields_ = [("device_buf", ct.c_void_p), ("k_begin", ct.c_int64), ("k_end", ct.c_int64),
                 ("t_begin", ct.c_int32), ("t_end", ct.c_int32)]
+
+
+class ac_batch_item(ct.Structure):
+    _fields_ = [("stream_id", ct.c_uint32), ("first_iter", ct.c_int32), ("n_iter", ct.c_int32),
+                ("update_last", ct.c_int32)]
 
 
 class ac_localize_params(ct.Structure):
@@ -69,7 +75,7 @@ _SIGS = {
     "ac_contour_count": (ct.c_int64, [ct.c_void_p]),
     "ac_destroy_contours": (None, [ct.c_void_p]),
     "ac_evolve": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_evolve_params), ct.POINTER(ac_trace), ct.c_void_p]),
-    "ac_evolve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_uint32), ct.c_int32,
+    "ac_evolve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ac_batch_item), ct.c_int32,
                                    ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_localize": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_localize_params), ct.c_void_p, ct.c_int64,
                                ct.POINTER(ct.c_int64), ct.c_void_p]),
@@ -259,6 +265,7 @@ class EvolveParams:
     first_iter: int = 0
     update_last: int = 0
     sampling: int = 0
+    halo_factor: float = 0.0
 
     def to_c(self) -> ac_evolve_params:
         p = ac_evolve_params()
@@ -299,16 +306,25 @@ def ac_evolve(ctr: Contours, params: EvolveParams, trace=None, stream=None):
                        ct.c_void_p(_stream(stream))))
 
 
-def ac_evolve_batch(sets, params: EvolveParams, stream_ids=None, stream=None):
-    """One launch over several contour sets; set i uses Philox counter word
-    stream_ids[i] (default params.stream_id) and the shared key params.seed."""
-    l = load()
+def _handles(sets):
+    return (ct.c_void_p * len(sets))(*[s.handle.value if isinstance(s.handle, ct.c_void_p) else s.handle for s in sets])
+
+
+def _items(items, n):
+    if items is None:
+        return None
+    arr = (ac_batch_item * n)()
+    for i, it in enumerate(items):
+        arr[i].stream_id, arr[i].first_iter, arr[i].n_iter, arr[i].update_last = (int(v) for v in it)
+    return arr
+
+
+def ac_evolve_batch(sets, params: EvolveParams, items=None, stream=None):
+    """One launch over several contour sets.  ``items``: None or per set
+    (stream_id, first_iter, n_iter, update_last); the Philox key is params.seed."""
     p = params.to_c()
-    arr = (ct.c_void_p * len(sets))(*[s.handle.value if isinstance(s.handle, ct.c_void_p) else s.handle for s in sets])
-    sd = None
-    if stream_ids is not None:
-        sd = (ct.c_uint32 * len(sets))(*[int(s) for s in stream_ids])
-    _check(l.ac_evolve_batch(arr, sd, len(sets), ct.byref(p), ct.c_void_p(_stream(stream))))
+    _check(load().ac_evolve_batch(_handles(sets), _items(items, len(sets)), len(sets), ct.byref(p),
+                                  ct.c_void_p(_stream(stream))))
 
 
 def ac_localize(ctr: Contours, E0: float, cap: int | None = None, stream=None) -> np.ndarray:

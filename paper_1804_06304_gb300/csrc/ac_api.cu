@@ -419,11 +419,14 @@ ac_status check_params(const ac_evolve_params *p)
     if (!(p->eps0 >= 0.0f) || !std::isfinite(p->eps0)) AC_FAIL(AC_ERR_ARG, "ac_evolve: eps0 must be >= 0");
     if (p->path != AC_PATH_BRICK && p->path != AC_PATH_PLAIN) AC_FAIL(AC_ERR_ARG, "ac_evolve: unknown path");
     if (p->sampling < 0 || p->sampling > 2) AC_FAIL(AC_ERR_ARG, "ac_evolve: sampling must be 0, 1 or 2");
+    if (!(p->halo_factor >= 0.0f) || p->halo_factor > 64.0f) AC_FAIL(AC_ERR_ARG, "ac_evolve: halo_factor in [0, 64]");
     if (p->first_iter < 0 || (int64_t)(p->first_iter ? p->first_iter : 1) + p->T > (1 << 30))
         AC_FAIL(AC_ERR_ARG, "ac_evolve: first_iter out of range");
-    if (p->lanes_per_contour != 0 && p->lanes_per_contour != 8 && p->lanes_per_contour != 16 &&
-        p->lanes_per_contour != 32)
-        AC_FAIL(AC_ERR_ARG, "ac_evolve: lanes_per_contour must be 0, 8, 16 or 32");
+    if (p->lanes_per_contour != 0 && p->lanes_per_contour != 4 && p->lanes_per_contour != 8 &&
+        p->lanes_per_contour != 16 && p->lanes_per_contour != 32)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: lanes_per_contour must be 0, 4, 8, 16 or 32");
+    if (p->lanes_per_contour == 4 && (p->compensated == 0 || p->sampling == 1 || (p->sampling == 0 && p->N < 64)))
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: 4 lanes per contour are built for compensated sums and fast sampling");
     if (p->warps_per_block < 0 || p->warps_per_block > 16) AC_FAIL(AC_ERR_ARG, "ac_evolve: warps_per_block in [0, 16]");
     if (p->path == AC_PATH_PLAIN && p->warps_per_block > 8) AC_FAIL(AC_ERR_ARG, "ac_evolve: plain path takes at most 8 warps per block");
     for (int d = 0; d < 3; ++d)
@@ -443,24 +446,33 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     pl.comp = p->compensated != 0;
     pl.acc = p->sampling == 1 || (p->sampling == 0 && p->N < 64);
     if (pl.acc && !pl.comp) AC_FAIL(AC_ERR_ARG, "ac_evolve: accurate sampling is built with compensated sums only");
-    // lanes per contour: about 16 samples per lane, 8..32 lanes
+    // lanes per contour: about 32 samples per lane (4 lanes only with compensated
+    // sums and fast sampling, otherwise at least 8), at most 32
     int G = p->lanes_per_contour;
     if (G == 0) {
-        G = 8;
-        while (G < 32 && (int64_t)G * 16 < p->N) G *= 2;
+        if (vol->ndim == 3) {   // 3D: a warp per contour unless N is small (measured best at N = 512)
+            G = 8;
+            while (G < 32 && (int64_t)G * 8 < p->N) G *= 2;
+        } else {
+            G = (pl.comp && !pl.acc) ? 4 : 8;
+            while (G < 32 && (int64_t)G * 32 < p->N) G *= 2;
+        }
     }
     pl.G = G;
     pl.warps = p->warps_per_block ? p->warps_per_block : 8;
     pl.quad_off = 0;
     if (!pl.brick) return AC_OK;
     const int al = 16 / vol->es;
-    const int64_t budget = 200 * 1024;
+    // 3D regions are kept within half the shared memory so two CTAs share an SM
+    const int64_t budget = vol->ndim == 3 ? 110 * 1024 : 200 * 1024;
     int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
     for (int d = 0; d < vol->ndim; ++d) {
-        const double cells = vol->ndim == 3 ? 2.0 : 8.0;
+        // lattice cells per brick: 2x2x2 in 3D, 12x8 in 2D (measured best for 128 samples)
+        const double cells = vol->ndim == 3 ? 2.0 : (d == 0 ? 12.0 : 8.0);
         B[d] = p->brick[d] ? p->brick[d] : (int)std::lround(cells * stride_hint / vol->sp[d]);
         B[d] = std::max(1, std::min(B[d], (int)std::min<int64_t>(vol->n[d], 224)));
-        h[d] = (int)std::ceil((2.5 * r_hint + 0.5 * p->dR) / vol->sp[d]) + 2;
+        const double hf = p->halo_factor > 0.0f ? p->halo_factor : (vol->ndim == 3 ? 2.5 : 3.5);
+        h[d] = (int)std::ceil((hf * r_hint + 0.5 * p->dR) / vol->sp[d]) + 2;
     }
     for (int iter = 0; iter < 4096; ++iter) {
         int64_t raw = vol->es;
@@ -481,9 +493,10 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
             raw *= ext;
         }
         int64_t quad_off = 0, total = raw;
-        if (vol->ndim == 2) {   // float4 quads after the raw region
+        if (vol->ndim == 2) {   // quads after the raw region: 4 halves (uint8, binary16) or float4
+            const int qbytes = (vol->dtype == AC_U8 || vol->dtype == AC_F16) ? 8 : 16;
             quad_off = (raw + 127) / 128 * 128;
-            total = quad_off + (int64_t)(pl.ext[0] - 1) * (pl.ext[1] - 1) * 16;
+            total = quad_off + (int64_t)(pl.ext[0] - 1) * (pl.ext[1] - 1) * qbytes;
         }
         if (fits_box && total <= budget) {
             pl.raw = (int)raw;
@@ -578,7 +591,7 @@ cudaError_t launch_evolve(ac_dtype t, const EvolveArgs &a, const Plan &pl, int64
 }
 
 // Shared by ac_evolve and ac_evolve_batch.  sets[0] owns the scratch buffers.
-ac_status evolve_sets(ac_contours *const *sets, const uint32_t *streams, int n_sets, const ac_evolve_params *p,
+ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int n_sets, const ac_evolve_params *p,
                       const ac_trace *trace, cudaStream_t st)
 {
     ac_status s = check_params(p);
@@ -609,6 +622,18 @@ ac_status evolve_sets(ac_contours *const *sets, const uint32_t *streams, int n_s
     a.first_iter = p->first_iter ? p->first_iter : 1;
     a.last_iter = a.first_iter + p->T - 1;
     a.update_last = p->update_last ? 1 : 0;
+    if (items) {   // the launch spans every set's window (plain path: one launch per n)
+        int lo = 1 << 30, hi = 0;
+        for (int i = 0; i < n_sets; ++i) {
+            if (items[i].first_iter < 1 || items[i].n_iter < 0 || (int64_t)items[i].first_iter + items[i].n_iter > (1 << 30))
+                AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: item iterations out of range");
+            if (items[i].n_iter == 0) continue;
+            lo = std::min(lo, items[i].first_iter);
+            hi = std::max(hi, items[i].first_iter + items[i].n_iter - 1);
+        }
+        a.first_iter = lo;
+        a.last_iter = hi;
+    }
     {
         // Philox round keys and the weight-band constants of Eq. 5 (launch constants)
         uint32_t k0 = (uint32_t)p->seed, k1 = (uint32_t)(p->seed >> 32);
@@ -654,7 +679,10 @@ ac_status evolve_sets(ac_contours *const *sets, const uint32_t *streams, int n_s
     std::vector<VolDesc> desc(n_sets);
     int64_t bricks = 0, cbase = 0;
     for (int i = 0; i < n_sets; ++i) {
-        desc[i] = make_desc(sets[i], streams ? streams[i] : p->stream_id);
+        desc[i] = make_desc(sets[i], items ? items[i].stream_id : p->stream_id);
+        desc[i].first_iter = items ? items[i].first_iter : a.first_iter;
+        desc[i].last_iter = items ? items[i].first_iter + items[i].n_iter - 1 : a.last_iter;
+        desc[i].update_last = items ? (items[i].update_last ? 1 : 0) : a.update_last;
         desc[i].contour_base = cbase;
         cbase += sets[i]->C;
         if (pl.brick) {
@@ -897,6 +925,9 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
     a.path_counts = ctr.path_counts;
 
     VolDesc desc = make_desc(&ctr, p->stream_id);
+    desc.first_iter = a.first_iter;
+    desc.last_iter = a.last_iter;
+    desc.update_last = a.update_last;
     int64_t bricks = 1;
     if (brick)
         for (int d = 0; d < 3; ++d) {
@@ -979,12 +1010,12 @@ extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params,
     return evolve_sets(&ctr, nullptr, 1, params, trace, (cudaStream_t)cuda_stream);
 }
 
-extern "C" ac_status ac_evolve_batch(ac_contours *const *sets, const uint32_t *stream_ids, int32_t n_sets,
+extern "C" ac_status ac_evolve_batch(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
                                      const ac_evolve_params *params, void *cuda_stream)
 {
     g_err.clear();
     if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: need 1..4096 sets");
-    return evolve_sets(sets, stream_ids, n_sets, params, nullptr, (cudaStream_t)cuda_stream);
+    return evolve_sets(sets, items, n_sets, params, nullptr, (cudaStream_t)cuda_stream);
 }
 
 extern "C" ac_status ac_evolve_stats(ac_contours *ctr, int64_t counts[3], void *cuda_stream)

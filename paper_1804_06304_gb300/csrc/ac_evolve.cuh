@@ -106,9 +106,40 @@ __device__ __forceinline__ void fast_axis(float x, float M, int &idx, float &fr)
     idx = (int)__float_as_uint(t) - 0x4B000000;
 }
 
-// 2D region as float4 quads (v[y][x], v[y][x+1], v[y+1][x], v[y+1][x+1]).
-struct QuadFast {
-    const float4 *Q;
+// 2D region as quads (v[y][x], v[y][x+1], v[y+1][x], v[y+1][x+1]): four halves
+// (8 bytes) for uint8 and binary16 voxels, which half precision holds exactly,
+// float4 otherwise.  One shared-memory load feeds a bilinear sample.
+struct HQuad {
+    __half2 lo, hi;   // (v00, v10), (v01, v11)
+};
+template <typename T> struct QuadOf { using type = float4; };
+template <> struct QuadOf<uint8_t> { using type = HQuad; };
+template <> struct QuadOf<__half> { using type = HQuad; };
+
+__device__ __forceinline__ float4 quad_f(const float4 &q) { return q; }
+__device__ __forceinline__ float4 quad_f(const HQuad &q)
+{
+    const float2 a = __half22float2(q.lo), b = __half22float2(q.hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <typename QT> __device__ __forceinline__ QT make_quad(float a, float b, float c, float d);
+template <> __device__ __forceinline__ float4 make_quad<float4>(float a, float b, float c, float d)
+{
+    return make_float4(a, b, c, d);
+}
+template <> __device__ __forceinline__ HQuad make_quad<HQuad>(float a, float b, float c, float d)
+{
+    return HQuad{__floats2half2_rn(a, b), __floats2half2_rn(c, d)};
+}
+
+__device__ __forceinline__ float quad_lerp(const float4 q, float f0, float f1)
+{
+    const float a0 = fmaf(f0, q.y - q.x, q.x), a1 = fmaf(f0, q.w - q.z, q.z);
+    return fmaf(f1, a1 - a0, a0);
+}
+
+template <typename QT> struct QuadFast {
+    const QT *Q;
     int qp;          // quads per row
     float M[2];
     __device__ __forceinline__ float at(float x0, float x1, float) const
@@ -117,9 +148,7 @@ struct QuadFast {
         float f0, f1;
         fast_axis(x0, M[0], i0, f0);
         fast_axis(x1, M[1], i1, f1);
-        const float4 q = Q[i1 * qp + i0];
-        const float a0 = fmaf(f0, q.y - q.x, q.x), a1 = fmaf(f0, q.w - q.z, q.z);
-        return fmaf(f1, a1 - a0, a0);
+        return quad_lerp(quad_f(Q[i1 * qp + i0]), f0, f1);
     }
 };
 
@@ -174,9 +203,8 @@ template <int DIM, typename T, bool QUAD> struct SmemClamp {
         axis_tap(ax[1], x1, b1, f1);
         if (DIM == 3) axis_tap(ax[2], x2, b2, f2);
         if (QUAD) {
-            const float4 q = reinterpret_cast<const float4 *>(p)[(o[1] + b1) * py + (o[0] + b0)];
-            const float a0 = fmaf(f0, q.y - q.x, q.x), a1 = fmaf(f0, q.w - q.z, q.z);
-            return fmaf(f1, a1 - a0, a0);
+            using QT = typename QuadOf<T>::type;
+            return quad_lerp(quad_f(reinterpret_cast<const QT *>(p)[(o[1] + b1) * py + (o[0] + b0)]), f0, f1);
         }
         const T *q = reinterpret_cast<const T *>(p) + (o[0] + b0) + (o[1] + b1) * py + (DIM == 3 ? (o[2] + b2) * pz : 0);
         return interp<DIM, T>(q, py, pz, f0, f1, f2, SmemLoad<T>());
@@ -202,11 +230,16 @@ template <int DIM, typename T> struct GlobalClamp {
 };
 
 // ----------------------------------------------------------------- one sample
-// Weights of Eq. 5 (four regions; linear bands of widths dr and dR) and the five
-// sums J = sum S I, J_R = sum dS/dR I, J_c = sum -S'(r) (raw direction) I.
-template <int DIM, bool COMP>
-__device__ __forceinline__ void accumulate(const IterC<DIM> &ic, const EvolveArgs &a, float rv, float I, float d0,
-                                           float d1, float d2, KSum *acc)
+// Weights of Eq. 5 (four regions; linear bands of widths dr and dR) and the terms
+// of the five sums J = sum S I, J_R = sum dS/dR I, J_c = sum -S'(r) (raw
+// direction) I for one sample.
+struct Terms {
+    float v[5];
+};
+
+template <int DIM>
+__device__ __forceinline__ Terms sample_terms(const IterC<DIM> &ic, const EvolveArgs &a, float rv, float I, float d0,
+                                              float d1, float d2)
 {
     const float t1 = fmaf(rv, ic.A1, ic.B1), t2 = fmaf(rv, ic.A2, ic.B2);
     const float r1 = __saturatef(t1), r2 = __saturatef(t2);
@@ -214,18 +247,33 @@ __device__ __forceinline__ void accumulate(const IterC<DIM> &ic, const EvolveArg
     const bool b1 = r1 == t1, b2 = r2 == t2;   // sample inside the inner / outer band
     const float dSdR = (b1 ? a.kR1 : 0.0f) + (b2 ? a.kR2 : 0.0f);
     const float g = ((b1 ? a.kr1 : 0.0f) + (b2 ? a.kr2 : 0.0f)) * I;
-    if (COMP) {
-        kadd(acc[0], S * I);
-        kadd(acc[1], dSdR * I);
-        kadd(acc[2], g * d0);
-        kadd(acc[3], g * d1);
-        if (DIM == 3) kadd(acc[4], g * d2);
-    } else {
-        acc[0].s = fmaf(S, I, acc[0].s);
-        acc[1].s = fmaf(dSdR, I, acc[1].s);
-        acc[2].s = fmaf(g, d0, acc[2].s);
-        acc[3].s = fmaf(g, d1, acc[3].s);
-        if (DIM == 3) acc[4].s = fmaf(g, d2, acc[4].s);
+    Terms t;
+    t.v[0] = S * I;
+    t.v[1] = dSdR * I;
+    t.v[2] = g * d0;
+    t.v[3] = g * d1;
+    t.v[4] = DIM == 3 ? g * d2 : 0.0f;
+    return t;
+}
+
+// Adds the terms of one or two samples: the pair is summed in one rounding, then
+// added with Kahan compensation (COMP) or plainly.
+template <int DIM, bool COMP>
+__device__ __forceinline__ void add_terms(KSum *acc, const Terms &x)
+{
+#pragma unroll
+    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) {
+        if (COMP) kadd(acc[i], x.v[i]);
+        else acc[i].s += x.v[i];
+    }
+}
+template <int DIM, bool COMP>
+__device__ __forceinline__ void add_terms(KSum *acc, const Terms &x, const Terms &y)
+{
+#pragma unroll
+    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) {
+        if (COMP) kadd(acc[i], x.v[i] + y.v[i]);
+        else acc[i].s += x.v[i] + y.v[i];
     }
 }
 
@@ -249,48 +297,60 @@ __device__ __forceinline__ void raw_direction2(uint32_t wa, float &d0, float &d1
     }
 }
 
+template <int DIM, bool ACC, typename Gather>
+__device__ __forceinline__ Terms sample3(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a, uint32_t j,
+                                         uint32_t n, uint32_t k, uint32_t stream)
+{
+    const uint4 w = philox4x32_10(make_uint4(j, n, k, stream), a.rk0, a.rk1);
+    const float u0 = top24(w.x) * 5.9604644775390625e-8f;
+    const float rv = ACC ? cbrtf(u0) : ex2_approx(lg2_approx(u0) * (1.0f / 3.0f));
+    const float t = top24(w.y) * 5.9604644775390625e-8f;
+    const float cphi = fmaf(-2.0f, t, 1.0f);
+    const float sh = ACC ? sqrtf(t * (1.0f - t)) : sqrt_approx(t * (1.0f - t));
+    float c0, s0;
+    raw_direction2<DIM, ACC>(w.z, c0, s0);
+    const float d0 = sh * c0, d1 = sh * s0;
+    const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
+    const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
+    const float x2 = fmaf(rv * ic.K[2], cphi, ic.ax[2].cf);
+    return sample_terms<DIM>(ic, a, rv, gat.at(x0, x1, x2), d0, d1, cphi);
+}
+
+template <int DIM, bool ACC, typename Gather>
+__device__ __forceinline__ Terms sample2(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a, uint32_t wr,
+                                         uint32_t wa)
+{
+    const float rv = ACC ? sqrtf(top24(wr)) : sqrt_approx(top24(wr));
+    float d0, d1;
+    raw_direction2<DIM, ACC>(wa, d0, d1);
+    const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
+    const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
+    return sample_terms<DIM>(ic, a, rv, gat.at(x0, x1, 0.0f), d0, d1, 0.0f);
+}
+
 template <int DIM, int G, bool COMP, bool ACC, typename Gather>
 __device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a,
                                                uint32_t n, uint32_t k, uint32_t stream, int lig, KSum *acc)
 {
     if constexpr (DIM == 3) {
-#pragma unroll 2
-        for (int j = lig; j < a.N; j += G) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)j, n, k, stream), a.rk0, a.rk1);
-            const float u0 = top24(w.x) * 5.9604644775390625e-8f;
-            const float rv = ACC ? cbrtf(u0) : ex2_approx(lg2_approx(u0) * (1.0f / 3.0f));
-            const float t = top24(w.y) * 5.9604644775390625e-8f;
-            const float cphi = fmaf(-2.0f, t, 1.0f);
-            const float sh = ACC ? sqrtf(t * (1.0f - t)) : sqrt_approx(t * (1.0f - t));
-            float c0, s0;
-            raw_direction2<DIM, ACC>(w.z, c0, s0);
-            const float d0 = sh * c0, d1 = sh * s0;
-            const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
-            const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
-            const float x2 = fmaf(rv * ic.K[2], cphi, ic.ax[2].cf);
-            accumulate<DIM, COMP>(ic, a, rv, gat.at(x0, x1, x2), d0, d1, cphi, acc);
+        // samples j and j + G of this lane form a pair
+        for (int j = lig; j < a.N; j += 2 * G) {
+            const Terms x = sample3<DIM, ACC>(gat, ic, a, (uint32_t)j, n, k, stream);
+            if (j + G < a.N) add_terms<DIM, COMP>(acc, x, sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + G), n, k, stream));
+            else add_terms<DIM, COMP>(acc, x);
         }
     } else {
-        const int blocks = (a.N + 1) >> 1;
-#pragma unroll 2
-        for (int m = lig; m < blocks; m += G) {
+        // the two samples of a Philox block form a pair; an odd N leaves one sample
+        // of the last block, handled after the loop
+        const int pairs = a.N >> 1;
+#pragma unroll 1
+        for (int m = lig; m < pairs; m += G) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
-            {
-                const float rv = ACC ? sqrtf(top24(w.x)) : sqrt_approx(top24(w.x));
-                float d0, d1;
-                raw_direction2<DIM, ACC>(w.y, d0, d1);
-                const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
-                const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
-                accumulate<DIM, COMP>(ic, a, rv, gat.at(x0, x1, 0.0f), d0, d1, 0.0f, acc);
-            }
-            if (2 * m + 1 < a.N) {
-                const float rv = ACC ? sqrtf(top24(w.z)) : sqrt_approx(top24(w.z));
-                float d0, d1;
-                raw_direction2<DIM, ACC>(w.w, d0, d1);
-                const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
-                const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
-                accumulate<DIM, COMP>(ic, a, rv, gat.at(x0, x1, 0.0f), d0, d1, 0.0f, acc);
-            }
+            add_terms<DIM, COMP>(acc, sample2<DIM, ACC>(gat, ic, a, w.x, w.y), sample2<DIM, ACC>(gat, ic, a, w.z, w.w));
+        }
+        if ((a.N & 1) && lig == pairs % G) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, n, k, stream), a.rk0, a.rk1);
+            add_terms<DIM, COMP>(acc, sample2<DIM, ACC>(gat, ic, a, w.x, w.y));
         }
     }
 }
@@ -408,7 +468,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ unsigned int s_paths[3];
+    using QT = typename QuadOf<T>::type;
 
     const int64_t b = blockIdx.x;
     const int64_t cb = lower_bound_u32(a.sorted_brick, a.total_contours, (uint32_t)b);
@@ -426,10 +486,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
     const int r0[3] = {max(0, bxi * a.B[0] - a.halo[0]) / AL * AL, max(0, byi * a.B[1] - a.halo[1]),
                        DIM == 3 ? max(0, bzi * a.B[2] - a.halo[2]) : 0};
 
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar, 1);
-        s_paths[0] = s_paths[1] = s_paths[2] = 0;
-    }
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(&mbar, (uint32_t)a.raw_bytes);
@@ -442,14 +499,14 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
     }
     const T *reg = reinterpret_cast<const T *>(smem_raw);
     const bool quad = DIM == 2 && a.quad_off > 0;
-    float4 *Q = reinterpret_cast<float4 *>(smem_raw + a.quad_off);
+    QT *Q = reinterpret_cast<QT *>(smem_raw + a.quad_off);
     const int qp = a.ext[0] - 1;
     if (quad) {
         const int nq = qp * (a.ext[1] - 1);
         for (int i = threadIdx.x; i < nq; i += blockDim.x) {
             const int y = i / qp, x = i - y * qp;
             const T *r = reg + y * a.ext[0] + x;
-            Q[i] = make_float4(to_f<T>(r[0]), to_f<T>(r[1]), to_f<T>(r[a.ext[0]]), to_f<T>(r[a.ext[0] + 1]));
+            Q[i] = make_quad<QT>(to_f<T>(r[0]), to_f<T>(r[1]), to_f<T>(r[a.ext[0]]), to_f<T>(r[a.ext[0] + 1]));
         }
         __syncthreads();
     }
@@ -460,13 +517,14 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
     const int ngrp = blockDim.x / G;
     const unsigned mask = group_mask<G>();
     const int64_t C = V.C;
+    unsigned int n_fast = 0, n_clamped = 0, n_global = 0;   // this group's contour-iterations per gather path
 
     for (int64_t i = cb + grp; i < ce; i += ngrp) {
         const int64_t k = (int64_t)a.sorted_gidx[i] - V.contour_base;
         float c[3] = {V.state[k], V.state[C + k], DIM == 3 ? V.state[2 * C + k] : 0.0f};
         float R = V.state[3 * C + k];
         Step s;
-        for (int n = a.first_iter; n <= a.last_iter; ++n) {
+        for (int n = V.first_iter; n <= V.last_iter; ++n) {
             IterC<DIM> ic;
             iter_consts<DIM>(ic, c, R, V, a);
             // where do the taps of the whole ball fall (clamped like the samples)?
@@ -484,11 +542,13 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
                 inside = inside && tlo >= r0[d] && thi < r0[d] + a.ext[d];
             }
             const int o[3] = {ic.ax[0].ci - r0[0], ic.ax[1].ci - r0[1], DIM == 3 ? ic.ax[2].ci - r0[2] : 0};
-            if (lig == 0) atomicAdd_block(&s_paths[inside ? (interior ? 0 : 1) : 2], 1u);
+            n_fast += (inside && interior) ? 1u : 0u;
+            n_clamped += (inside && !interior) ? 1u : 0u;
+            n_global += inside ? 0u : 1u;
             if (inside && interior) {
                 const float M[3] = {8388608.0f + (float)o[0], 8388608.0f + (float)o[1], 8388608.0f + (float)o[2]};
                 if (quad) {
-                    QuadFast gat{Q, qp, {M[0], M[1]}};
+                    QuadFast<QT> gat{Q, qp, {M[0], M[1]}};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 } else {
                     RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}};
@@ -512,7 +572,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
                 if (lig == 0) atomicOr(a.status, STATUS_NONFINITE);
                 break;
             }
-            if (n < a.last_iter || a.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
+            if (n < V.last_iter || V.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
         }
         if (lig == 0) {
             V.state[k] = c[0];
@@ -524,8 +584,13 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
                 atomicOr(a.status, STATUS_NONFINITE);
         }
     }
-    __syncthreads();
-    if (threadIdx.x < 3 && s_paths[threadIdx.x]) atomicAdd(&a.path_counts[threadIdx.x], (unsigned long long)s_paths[threadIdx.x]);
+    // one atomic per warp and path: sum the groups' counts over the warp
+    const unsigned int cnt[3] = {n_fast, n_clamped, n_global};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const unsigned int tot = __reduce_add_sync(0xffffffffu, lig == 0 ? cnt[p] : 0u);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.path_counts[p], (unsigned long long)tot);
+    }
 }
 
 // ----------------------------------------------------------------- plain kernel
@@ -534,9 +599,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
 template <int DIM, typename T, int G, bool COMP, bool ACC>
 __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant__ EvolveArgs a)
 {
-    __shared__ unsigned int s_glob;
-    if (threadIdx.x == 0) s_glob = 0;
-    __syncthreads();
+    unsigned int glob = 0;
     const int lig = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
@@ -544,6 +607,7 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
     for (int64_t gi = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G; gi < a.total_contours; gi += groups) {
         const int v = find_vol(a, gi, false);
         const VolDesc &V = a.vols[v];
+        if (n < V.first_iter || n > V.last_iter) continue;   // outside this set's iterations
         const int64_t k = gi - V.contour_base;
         const int64_t C = V.C;
         float c[3] = {V.state[k], V.state[C + k], DIM == 3 ? V.state[2 * C + k] : 0.0f};
@@ -554,10 +618,10 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
                                 {ic.ax[0], ic.ax[1], ic.ax[2]}};
         const Step s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
         if (lig == 0) {
-            atomicAdd_block(&s_glob, 1u);
+            ++glob;
             write_trace(a, v, k, n, c, R, s);
             if (!finite_step(s)) atomicOr(a.status, STATUS_NONFINITE);
-            else if (n < a.last_iter || a.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
+            else if (n < V.last_iter || V.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
             V.state[k] = c[0];
             V.state[C + k] = c[1];
             if (DIM == 3) V.state[2 * C + k] = c[2];
@@ -567,8 +631,8 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
                 atomicOr(a.status, STATUS_NONFINITE);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && s_glob) atomicAdd(&a.path_counts[2], (unsigned long long)s_glob);
+    const unsigned int tot = __reduce_add_sync(0xffffffffu, glob);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.path_counts[2], (unsigned long long)tot);
 }
 
 // ----------------------------------------------------------------- launchers
@@ -589,8 +653,9 @@ cudaError_t launch_plain_t(const EvolveArgs &a, int warps, int64_t grid, cudaStr
     return cudaGetLastError();
 }
 
-// Instantiated combinations: every lane count with compensated sums in the fast
-// and the accurate sampling mode, and plain FP32 sums in the fast mode.
+// Instantiated combinations: 8, 16 and 32 lanes with compensated sums in the fast
+// and the accurate sampling mode and with plain FP32 sums in the fast mode, and 4
+// lanes with compensated sums in the fast mode.
 template <typename T>
 cudaError_t launch_evolve_t(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                             cudaStream_t st)
@@ -602,6 +667,7 @@ cudaError_t launch_evolve_t(const EvolveArgs &a, bool brick, int G, bool comp, b
 #define AC_DISPATCH_G(DIM, CC, AA) AC_DISPATCH(DIM, 32, CC, AA) AC_DISPATCH(DIM, 16, CC, AA) AC_DISPATCH(DIM, 8, CC, AA)
     AC_DISPATCH_G(3, true, false) AC_DISPATCH_G(3, false, false) AC_DISPATCH_G(3, true, true)
     AC_DISPATCH_G(2, true, false) AC_DISPATCH_G(2, false, false) AC_DISPATCH_G(2, true, true)
+    AC_DISPATCH(2, 4, true, false) AC_DISPATCH(3, 4, true, false)
 #undef AC_DISPATCH_G
 #undef AC_DISPATCH
     return cudaErrorInvalidValue;

@@ -35,7 +35,9 @@ struct VolDesc {
     int64_t brick_base;  // first global brick index of this set
     int64_t contour_base;// first global contour index of this set
     uint32_t stream;     // fourth Philox counter word of this set
-    uint32_t pad_;
+    int32_t first_iter;  // iterations of this set: first_iter .. last_iter
+    int32_t last_iter;
+    int32_t update_last; // update after last_iter too
 };
 
 struct EvolveArgs {
@@ -82,9 +84,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, con
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;   // one 32x32->64 multiply each
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r],
+                       (uint32_t)p0);
     }
     return c;
 }

@@ -69,11 +69,12 @@ def test_struct_layouts_match_header(ac, tmp_path):
     checks = {
         "ac_evolve_params": ["N", "T", "eps0", "dR", "Rmin", "Rmax", "max_step", "seed", "stream_id", "path",
                              "lanes_per_contour", "compensated", "brick", "warps_per_block", "first_iter",
-                             "update_last", "sampling"],
+                             "update_last", "sampling", "halo_factor"],
         "ac_trace": ["device_buf", "k_begin", "k_end", "t_begin", "t_end"],
         "ac_cell": ["c", "r", "E", "id"],
         "ac_seed_params": ["stride", "R0"],
         "ac_localize_params": ["E0"],
+        "ac_batch_item": ["stream_id", "first_iter", "n_iter", "update_last"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac.h"', "int main(void){"]
     for st, fields in checks.items():

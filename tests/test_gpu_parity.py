@@ -306,9 +306,44 @@ def test_batch_equals_single(ac):
         V = ac.ac_create_volume(s.volume)
         keep.append(V)
         sets.append(ac.ac_seed(V, stride=4.0))
-    ac.ac_evolve_batch(sets, p, stream_ids=[100 + i for i in range(len(vols))])
+    ac.ac_evolve_batch(sets, p, items=[(100 + i, 1, p.T, 0) for i in range(len(vols))])
     for c, want in zip(sets, singles):
         np.testing.assert_array_equal(ac.ac_get_state(c), want)
+
+
+def test_batch_sets_at_different_iterations(ac):
+    """Continuous batching: sets at different stages of their evolution share one
+    launch (per-set iteration windows) and each gives what it gives alone."""
+    from paper_1804_06304_gb300 import synth
+    vols = synth.batch_3d(5, count=3, max_scale=0.25)
+    p = ac.default_params(3, 4.0 / math.sqrt(1.5), 170.0, N=128, T=10)
+    alone, sets, keep = [], [], []
+    windows = [(7, 1, 10, 0), (8, 4, 6, 1), (9, 3, 0, 0)]   # (stream, first, n, update_last)
+    for s, (sid, f, nit, ul) in zip(vols, windows):
+        V = ac.ac_create_volume(s.volume)
+        C1 = ac.ac_seed(V, stride=4.0)
+        C2 = ac.ac_seed(V, stride=4.0)
+        if f > 1:   # bring both copies to iteration f with an uninterrupted prefix
+            pre = ac.EvolveParams(**{**p.__dict__, "stream_id": sid, "T": f - 1, "update_last": 1})
+            ac.ac_evolve(C1, pre)
+            ac.ac_evolve(C2, pre)
+        if nit > 0:
+            ac.ac_evolve(C1, ac.EvolveParams(**{**p.__dict__, "stream_id": sid, "first_iter": f, "T": nit,
+                                                "update_last": ul}))
+        alone.append(ac.ac_get_state(C1))
+        keep += [V, C1]
+        sets.append(C2)
+    ac.ac_evolve_batch(sets, p, items=windows)
+    for c, want in zip(sets, alone):
+        np.testing.assert_array_equal(ac.ac_get_state(c), want)
+    p2 = ac.EvolveParams(**{**p.__dict__, "path": 1})   # the plain path honours the windows too
+    for s, (sid, f, nit, ul), want in zip(vols, windows, alone):
+        V = ac.ac_create_volume(s.volume)
+        C = ac.ac_seed(V, stride=4.0)
+        if f > 1:
+            ac.ac_evolve(C, ac.EvolveParams(**{**p.__dict__, "stream_id": sid, "T": f - 1, "update_last": 1}))
+        ac.ac_evolve_batch([C], p2, items=[(sid, f, nit, ul)])
+        np.testing.assert_array_equal(ac.ac_get_state(C), want)
 
 
 def test_nonfinite_volume_is_reported(ac):
@@ -326,7 +361,8 @@ def test_invalid_parameters_rejected(ac, small3d):
     V = ac.ac_create_volume(small3d.volume)
     C = ac.ac_seed(V, stride=4.0)
     bad = [dict(N=0), dict(T=0), dict(dR=0.0), dict(Rmin=2.0, Rmax=1.0), dict(max_step=0.0),
-           dict(lanes_per_contour=4), dict(path=7), dict(eps0=float("nan")), dict(brick=(300, 8, 8))]
+           dict(lanes_per_contour=5), dict(lanes_per_contour=4, compensated=0), dict(path=7), dict(eps0=float("nan")),
+           dict(brick=(300, 8, 8)), dict(sampling=3), dict(halo_factor=-1.0), dict(warps_per_block=17)]
     for b in bad:
         p = _p3(ac, small3d, T=2)
         p = ac.EvolveParams(**{**p.__dict__, **b})

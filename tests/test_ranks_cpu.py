@@ -1,0 +1,67 @@
+"""The multi-rank host logic of bench.py on CPU (gloo, world size 2): images are
+independent replicas, so ranks exchange nothing but the step time, whose maximum
+sets the whole-job throughput.  The reference arm under torchrun prints one line
+from rank 0 only."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local = [10.0, 12.0] if rank == 0 else [30.0, 34.0]
+    t, v = bench.aggregate_ranks(local, 1000, world, bench.torch_max_reducer("cpu"))
+    q.put((rank, t, v))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_gloo():
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, v in out:
+        assert t == 32.0                          # max over ranks of the mean step time
+        assert abs(v - 2 * 1000 / 0.032) < 1e-6   # world x per-rank samples / max time
+
+
+def test_single_rank_aggregate():
+    sys.path.insert(0, ROOT)
+    import bench
+    t, v = bench.aggregate_ranks([2.0, 4.0], 500, 1)
+    assert t == 3.0 and abs(v - 500 / 0.003) < 1e-6
+
+
+@pytest.mark.slow
+def test_reference_arm_under_torchrun_prints_once():
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29517", "bench.py", "--impl", "reference",
+                        "--workload", "small-3d", "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
