@@ -60,6 +60,10 @@ WORKLOADS = {
     "small-3d": dict(ndim=3, stride=4.0, N=256, T=50, seed=0,
                      desc="64x64x32 uint8, 20 balls r 4-6, noise 15; stride-4 lattice (2048 contours), 256 samples, "
                           "50 iterations"),
+    "batch-3d": dict(ndim=3, stride=4.0, N=256, T=80, seed=3, count=64,
+                     desc="64 uint8 volumes 64^3..512x512x128 (log-uniform voxel count), 1 nucleus per 2000 voxels, "
+                          "r 3-8; stride-4 lattices; one autotuned plan over all volumes replayed as a CUDA graph; "
+                          "256 samples, 80 iterations"),
 }
 
 
@@ -68,6 +72,8 @@ def make_input(name: str, seed: int, dtype: str, size: int = 0):
     if name == "large-2d":
         side = size or 4096
         s = synth.large_2d(seed, shape=(side, side), n_nuclei=int(round(12_000 * side * side / 4096**2)))
+    elif name == "batch-3d":
+        raise ValueError("batch-3d has no single input")
     elif name == "brain-3d":
         side = size or 1024
         s = synth.brain_3d(seed, shape=(side, side, side // 4), n_nuclei=int(round(100_000 * (side / 1024) ** 3)),
@@ -166,6 +172,27 @@ def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0):
     return samples / dt, threads, f"{m} of {len(seeds)} contours (random, seed {rng_seed}), all {wl['T']} iterations"
 
 
+def oracle_sample_batch(vols, wl, seconds: float, rng_seed: int = 0):
+    """The oracle on random volumes of a batch, each through ``oracle_sample``, until
+    about `seconds` of evolution have run; returns (samples/s, threads, sample text)."""
+    rng = np.random.default_rng(rng_seed)
+    samples, spent, picked, threads = 0.0, 0.0, [], 0
+    while spent < seconds and len(picked) < 4 * len(vols):
+        i = int(rng.integers(len(vols)))
+        sv = vols[i]
+        t0 = time.perf_counter()
+        rate, threads, desc = oracle_sample(sv, sv.volume, wl, sv.spacing, max(0.5, seconds - spent),
+                                            rng_seed=int(rng.integers(1 << 30)))
+        wall = time.perf_counter() - t0
+        m = int(desc.split(" of ")[0])
+        samples += m * wl["N"] * wl["T"]
+        spent += m * wl["N"] * wl["T"] / rate
+        picked.append(f"volume {i}: {desc.split(' (')[0]}")
+        if wall > 2 * seconds:
+            break
+    return samples / spent, threads, "; ".join(picked) + f"; all {wl['T']} iterations"
+
+
 # ------------------------------------------------------------------------ ranks
 def aggregate_ranks(local_ms: list, samples_per_rank: int, world: int, reduce_max=None) -> tuple:
     """Whole-job throughput of independent replicas: each rank's mean step time,
@@ -228,6 +255,8 @@ def main(argv=None):
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "batch-3d":
+        return batch_arm(args, wl, rank, world, dev)
 
     s, vol = make_input(args.workload, wl["seed"] + rank, args.dtype, args.size)
     spacing = s.spacing
@@ -345,23 +374,137 @@ def main(argv=None):
         dist.destroy_process_group()
 
 
+def batch_arm(args, wl, rank, world, dev):
+    """Batching form: every step re-seeds the 64 volumes' lattices, replays one
+    CUDA graph holding the binning, sort and single evolution launch over all of
+    them, and localizes each volume."""
+    import torch
+    import torch.distributed as dist
+    from paper_1804_06304_gb300 import ac, synth
+
+    dist_on = world > 1
+    vols = synth.batch_3d(wl["seed"] + rank, count=wl["count"])
+    V, C = [], []
+    pinned = []
+    for sv in vols:
+        V.append(ac.ac_create_volume(sv.volume, sv.spacing))
+        C.append(ac.ac_seed(V[-1], stride=wl["stride"]))
+        pinned.append(torch.from_numpy(sv.volume).pin_memory())
+    R0 = wl["stride"] / math.sqrt(1.5)
+    params = ac.default_params(3, R0, 170.0, N=wl["N"], T=wl["T"], seed=1000 + rank, compensated=args.compensated)
+    t0 = time.perf_counter()
+    params = ac.ac_autotune(C, params)
+    tune_s = time.perf_counter() - t0
+    items = [(i, 1, wl["T"], 0) for i in range(len(C))]
+    plan = ac.ac_plan_create(C, params, items=items)
+    E0 = ac.default_E0(3, 170.0)
+    total = sum(c.count for c in C)
+    samples = total * wl["N"] * wl["T"]
+
+    def step(from_host=False):
+        if from_host:
+            for v, src in zip(V, pinned):
+                ac.ac_load_volume(v, src)
+        for c in C:
+            ac.ac_reseed(c)
+        ac.ac_plan_launch(plan, use_graph=True)
+        return sum(len(ac.ac_localize(c, E0)) for c in C)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist_on:
+        dist.barrier()
+    clocks = ClockSampler(None)
+    clocks.start()
+    ms, kms = [], []
+    launches0 = ac.ac_kernel_launches()
+    cells = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cells = step()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        kms.append(ac.ac_evolve_kernel_ms(C[0]))
+    launches = ac.ac_kernel_launches() - launches0
+    torch.cuda.synchronize()
+    if dist_on:
+        dist.barrier()
+    clk = clocks.stop()
+    reducer = torch_max_reducer(dev) if dist_on else None
+    t_ms, value = aggregate_ranks(ms, samples, world, reducer)
+    k_ms, _ = aggregate_ranks(kms, samples, world, reducer)
+    e2e = None
+    if not args.no_e2e:
+        ems = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(from_host=True)
+            e1.record()
+            e1.synchronize()
+            ems.append(e0.elapsed_time(e1))
+        e_ms, e_val = aggregate_ranks(ems, samples, world, reducer)
+        e2e = {"value": e_val, "unit": "samples/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(sum(sv.volume.nbytes for sv in vols)),
+               "d2h_bytes_per_step": int(cells * 24 + len(C) * 24)}
+    paths = ac.ac_evolve_stats(C[0])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, thr, desc = oracle_sample_batch(vols, wl, args.cpu_seconds)
+        cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc}
+    achieved = ALG_SLOTS_PER_SAMPLE[3] * samples / (k_ms * 1e-3) / 1e12
+    peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "MC contour samples/s (whole path: seed, evolve, localize; batching form)",
+            "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 arithmetic on uint8 voxels", "data": "synthetic",
+            "config": {"workload": "batch-3d", "desc": wl["desc"], "volumes": len(C), "contours": total,
+                       "voxels": int(sum(sv.volume.size for sv in vols)), "samples": wl["N"], "iterations": wl["T"],
+                       "autotuned": {"lanes_per_contour": params.lanes_per_contour, "brick": list(params.brick),
+                                     "warps_per_block": params.warps_per_block, "seconds": tune_s},
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "cells": cells, "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "evolve_brick_kernel (plan, graph)",
+                         "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[3]},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}))
+    if dist_on:
+        dist.destroy_process_group()
+
+
 def reference_arm(args, wl, rank, world):
     """The FP64 oracle timed on the host cores: each step a bounded random sample of
     the same workload's contours (all iterations)."""
     if rank != 0:
         return
-    s, vol = make_input(args.workload, wl["seed"], args.dtype, args.size)
     per_step = max(2.0, min(15.0, 120.0 / max(1, args.steps + args.warmup)))
+    if args.workload == "batch-3d":
+        from paper_1804_06304_gb300 import synth
+        vols = synth.batch_3d(wl["seed"], count=wl["count"])
+        run = lambda seed: oracle_sample_batch(vols, wl, per_step, rng_seed=seed)  # noqa: E731
+        C = sum(lattice_count(sv.shape_xyz, sv.spacing, wl["stride"], 3) for sv in vols)
+    else:
+        s, vol = make_input(args.workload, wl["seed"], args.dtype, args.size)
+        run = lambda seed: oracle_sample(s, vol, wl, s.spacing, per_step, rng_seed=seed)  # noqa: E731
+        C = lattice_count(s.shape_xyz, s.spacing, wl["stride"], wl["ndim"])
     for i in range(args.warmup):
-        oracle_sample(s, vol, wl, s.spacing, per_step, rng_seed=100 + i)
+        run(100 + i)
     vals, thr, desc = [], 0, ""
     t0 = time.perf_counter()
     for i in range(args.steps):
-        v, thr, desc = oracle_sample(s, vol, wl, s.spacing, per_step, rng_seed=i)
+        v, thr, desc = run(i)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = float(np.mean(vals))
-    C = lattice_count(s.shape_xyz, s.spacing, wl["stride"], wl["ndim"])
     line = {"impl": "reference", "metric": "MC contour samples/s (whole path: ingest, seed, evolve, localize)",
             "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

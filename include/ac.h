@@ -195,6 +195,36 @@ ac_status ac_evolve_batch(ac_contours *const *sets, const ac_batch_item *items, 
                           const ac_evolve_params *params, void *cuda_stream);
 
 /*
+ * Plans: a launch over fixed contour sets, planned once and launched many times
+ * (batching form).  ac_plan_create does the host work of ac_evolve_batch -- brick
+ * plan, descriptors, TMA descriptors, scratch -- and uploads it (synchronous).
+ * ac_plan_launch enqueues only device work: binning, sort, the evolution kernel;
+ * with use_graph = 1 that sequence is captured once into a CUDA graph and replayed
+ * on every later launch.  ac_plan_set_items changes the sets' iteration windows
+ * and stream words for later launches (a plain-path graph is recaptured when the
+ * iteration span changes).  The sets, their volumes and the plan's own buffers
+ * must stay alive and unmoved while the plan exists; launches on one plan are
+ * serialised by the caller's stream.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+typedef struct ac_plan ac_plan;
+ac_status ac_plan_create(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
+                         const ac_evolve_params *params, ac_plan **out);
+ac_status ac_plan_set_items(ac_plan *plan, const ac_batch_item *items, void *cuda_stream);
+ac_status ac_plan_launch(ac_plan *plan, int use_graph, void *cuda_stream);
+void ac_destroy_plan(ac_plan *plan);
+
+/*
+ * ac_autotune -- choose lanes_per_contour, brick and warps_per_block for these sets
+ * by timing short trial launches (3 iterations) of candidate configurations on
+ * copies of their state (the sets are not modified), and write them into
+ * *params.  A fixed lanes_per_contour is kept; the plain path is left untouched.
+ * Results are cached per workload shape (dimension, voxel type, N, summation and
+ * sampling mode, lattice spacing, radius, halo factor) for the process.
+ * Synchronizes the stream.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_evolve_params *params, void *cuda_stream);
+
+/*
  * ac_evolve_static -- ac_evolve for callers that cannot allocate device memory.
  * Some callers must not call cudaMalloc: code whose device memory is owned by
  * its own allocator (a framework's caching allocator that has reserved the free
@@ -278,9 +308,9 @@ ac_status ac_philox4x32_10(const uint32_t *ctr_dev, uint64_t key, uint32_t *out_
                            void *cuda_stream);
 
 /* Device time in milliseconds of the evolution kernel launch(es) of the last
- * ac_evolve / ac_evolve_batch on this handle (CUDA events recorded by the library
- * on the launching stream; binning and sorting excluded).  Synchronizes on the end
- * event.  Errors: AC_ERR_ARG, AC_ERR_STATE (nothing evolved yet), AC_ERR_CUDA. */
+ * ac_evolve / ac_evolve_batch / ac_plan_launch whose first set is this handle (CUDA
+ * events recorded by the library on the launching stream, inside the graph for a
+ * graph launch; binning and sorting excluded).  Synchronizes on the end event.  Errors: AC_ERR_ARG, AC_ERR_STATE (nothing evolved yet), AC_ERR_CUDA. */
 ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms);
 
 /* Contour-iterations of the last ac_evolve / ac_evolve_batch on this handle by

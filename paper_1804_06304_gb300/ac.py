@@ -89,6 +89,12 @@ _SIGS = {
     "ac_evolve_static": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
                                     ct.POINTER(ct.c_float), ct.c_float, ct.c_void_p, ct.c_int64, ct.c_float,
                                     ct.c_float, ct.POINTER(ac_evolve_params), ct.c_void_p]),
+    "ac_plan_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ac_batch_item), ct.c_int32,
+                                  ct.POINTER(ac_evolve_params), ct.POINTER(ct.c_void_p)]),
+    "ac_plan_set_items": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_batch_item), ct.c_void_p]),
+    "ac_plan_launch": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "ac_destroy_plan": (None, [ct.c_void_p]),
+    "ac_autotune": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int32, ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_last_error": (ct.c_char_p, []),
 }
 
@@ -325,6 +331,47 @@ def ac_evolve_batch(sets, params: EvolveParams, items=None, stream=None):
     p = params.to_c()
     _check(load().ac_evolve_batch(_handles(sets), _items(items, len(sets)), len(sets), ct.byref(p),
                                   ct.c_void_p(_stream(stream))))
+
+
+class Plan:
+    def __init__(self, handle, sets):
+        self.handle = handle
+        self.sets = list(sets)   # keep the contour sets alive
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ac_destroy_plan(self.handle)
+            self.handle = None
+
+
+def ac_plan_create(sets, params: EvolveParams, items=None) -> Plan:
+    out = ct.c_void_p()
+    p = params.to_c()
+    _check(load().ac_plan_create(_handles(sets), _items(items, len(sets)), len(sets), ct.byref(p), ct.byref(out)))
+    return Plan(out, sets)
+
+
+def ac_plan_set_items(plan: Plan, items, stream=None):
+    _check(load().ac_plan_set_items(plan.handle, _items(items, len(plan.sets)), ct.c_void_p(_stream(stream))))
+
+
+def ac_plan_launch(plan: Plan, use_graph: bool = True, stream=None):
+    _check(load().ac_plan_launch(plan.handle, int(use_graph), ct.c_void_p(_stream(stream))))
+
+
+def ac_destroy_plan(plan: Plan):
+    if plan.handle:
+        load().ac_destroy_plan(plan.handle)
+        plan.handle = None
+
+
+def ac_autotune(sets, params: EvolveParams, stream=None) -> EvolveParams:
+    """Returns a copy of ``params`` with lanes_per_contour, brick and
+    warps_per_block chosen by timed trials on copies of the sets' state."""
+    p = params.to_c()
+    _check(load().ac_autotune(_handles(sets), len(sets), ct.byref(p), ct.c_void_p(_stream(stream))))
+    return dataclasses.replace(params, lanes_per_contour=int(p.lanes_per_contour),
+                               warps_per_block=int(p.warps_per_block), brick=tuple(int(b) for b in p.brick))
 
 
 def ac_localize(ctr: Contours, E0: float, cap: int | None = None, stream=None) -> np.ndarray:

@@ -6,8 +6,11 @@
 #include <cmath>
 #include <cstring>
 #include <cub/cub.cuh>
+#include <array>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -590,9 +593,55 @@ cudaError_t launch_evolve(ac_dtype t, const EvolveArgs &a, const Plan &pl, int64
     }
 }
 
-// Shared by ac_evolve and ac_evolve_batch.  sets[0] owns the scratch buffers.
-ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int n_sets, const ac_evolve_params *p,
-                      const ac_trace *trace, cudaStream_t st)
+// A launch over one or more contour sets, planned on the host.
+struct Prepared {
+    Plan pl;
+    EvolveArgs a;
+    ac_dtype dtype = AC_U8;
+    int n_sets = 0;
+    int64_t total = 0, bricks = 0;
+    int end_bit = 1;
+    size_t cub_bytes = 0;
+    std::vector<VolDesc> desc;
+    std::vector<CUtensorMap> maps;
+    ac_contours *owner = nullptr;   // status word, path counters, kernel-time events
+};
+
+// Applies per-set iteration windows and stream words to the descriptors and the
+// launch's iteration span.
+ac_status apply_items(Prepared &pr, const ac_batch_item *items, const ac_evolve_params *p)
+{
+    EvolveArgs &a = pr.a;
+    a.first_iter = p->first_iter ? p->first_iter : 1;
+    a.last_iter = a.first_iter + p->T - 1;
+    a.update_last = p->update_last ? 1 : 0;
+    if (items) {   // the launch spans every set's window (plain path: one launch per n)
+        int lo = 1 << 30, hi = 0;
+        for (int i = 0; i < pr.n_sets; ++i) {
+            if (items[i].first_iter < 1 || items[i].n_iter < 0 ||
+                (int64_t)items[i].first_iter + items[i].n_iter > (1 << 30))
+                AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: item iterations out of range");
+            if (items[i].n_iter == 0) continue;
+            lo = std::min(lo, items[i].first_iter);
+            hi = std::max(hi, items[i].first_iter + items[i].n_iter - 1);
+        }
+        a.first_iter = lo;
+        a.last_iter = hi;
+    }
+    for (int i = 0; i < pr.n_sets; ++i) {
+        VolDesc &d = pr.desc[i];
+        d.stream = items ? items[i].stream_id : p->stream_id;
+        d.first_iter = items ? items[i].first_iter : a.first_iter;
+        d.last_iter = items ? items[i].first_iter + items[i].n_iter - 1 : a.last_iter;
+        d.update_last = items ? (items[i].update_last ? 1 : 0) : a.update_last;
+    }
+    return AC_OK;
+}
+
+// Host work of a launch: checks, plan, descriptors, tensor maps, scratch sizes;
+// uploads the descriptors and maps into `sc` on the stream.
+ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int n_sets, const ac_evolve_params *p,
+                       const ac_trace *trace, Scratch &sc, Prepared &pr, cudaStream_t st)
 {
     ac_status s = check_params(p);
     if (s != AC_OK) return s;
@@ -608,32 +657,21 @@ ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int 
         total += sets[i]->C;
     }
     if (total >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve: too many contours in one launch");
-    Plan pl;
+    Plan &pl = pr.pl;
     s = plan_evolve(v0, stride_hint, r_hint, p, pl);
     if (s != AC_OK) return s;
+    pr.dtype = v0->dtype;
+    pr.n_sets = n_sets;
+    pr.total = total;
+    pr.owner = sets[0];
 
-    EvolveArgs a;
+    EvolveArgs &a = pr.a;
     std::memset(&a, 0, sizeof(a));
     a.n_vols = n_sets;
     a.ndim = v0->ndim;
     a.total_contours = total;
     a.N = p->N;
     a.T = p->T;
-    a.first_iter = p->first_iter ? p->first_iter : 1;
-    a.last_iter = a.first_iter + p->T - 1;
-    a.update_last = p->update_last ? 1 : 0;
-    if (items) {   // the launch spans every set's window (plain path: one launch per n)
-        int lo = 1 << 30, hi = 0;
-        for (int i = 0; i < n_sets; ++i) {
-            if (items[i].first_iter < 1 || items[i].n_iter < 0 || (int64_t)items[i].first_iter + items[i].n_iter > (1 << 30))
-                AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: item iterations out of range");
-            if (items[i].n_iter == 0) continue;
-            lo = std::min(lo, items[i].first_iter);
-            hi = std::max(hi, items[i].first_iter + items[i].n_iter - 1);
-        }
-        a.first_iter = lo;
-        a.last_iter = hi;
-    }
     {
         // Philox round keys and the weight-band constants of Eq. 5 (launch constants)
         uint32_t k0 = (uint32_t)p->seed, k1 = (uint32_t)(p->seed >> 32);
@@ -662,6 +700,27 @@ ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int 
     }
     a.status = sets[0]->status;
     a.path_counts = sets[0]->path_counts;
+
+    pr.desc.assign(n_sets, VolDesc());
+    int64_t bricks = 0, cbase = 0;
+    for (int i = 0; i < n_sets; ++i) {
+        pr.desc[i] = make_desc(sets[i], p->stream_id);
+        pr.desc[i].contour_base = cbase;
+        cbase += sets[i]->C;
+        if (pl.brick) {
+            int64_t nb = 1;
+            for (int d = 0; d < 3; ++d) {
+                pr.desc[i].nb[d] = (int32_t)((sets[i]->vol->n[d] + pl.B[d] - 1) / pl.B[d]);
+                nb *= pr.desc[i].nb[d];
+            }
+            pr.desc[i].brick_base = bricks;
+            bricks += nb;
+        }
+    }
+    if (bricks >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve: too many bricks");
+    pr.bricks = bricks;
+    s = apply_items(pr, items, p);
+    if (s != AC_OK) return s;
     if (trace && trace->device_buf) {
         if (n_sets != 1) AC_FAIL(AC_ERR_ARG, "ac_evolve: trace is supported for a single set");
         if (trace->k_begin < 0 || trace->k_end > sets[0]->C || trace->k_begin > trace->k_end || trace->t_begin < 1 ||
@@ -675,91 +734,44 @@ ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int 
     }
     if (total == 0) return AC_OK;
 
-    Scratch &sc = sets[0]->scratch;
-    std::vector<VolDesc> desc(n_sets);
-    int64_t bricks = 0, cbase = 0;
-    for (int i = 0; i < n_sets; ++i) {
-        desc[i] = make_desc(sets[i], items ? items[i].stream_id : p->stream_id);
-        desc[i].first_iter = items ? items[i].first_iter : a.first_iter;
-        desc[i].last_iter = items ? items[i].first_iter + items[i].n_iter - 1 : a.last_iter;
-        desc[i].update_last = items ? (items[i].update_last ? 1 : 0) : a.update_last;
-        desc[i].contour_base = cbase;
-        cbase += sets[i]->C;
-        if (pl.brick) {
-            int64_t nb = 1;
-            for (int d = 0; d < 3; ++d) {
-                desc[i].nb[d] = (int32_t)((sets[i]->vol->n[d] + pl.B[d] - 1) / pl.B[d]);
-                nb *= desc[i].nb[d];
-            }
-            desc[i].brick_base = bricks;
-            bricks += nb;
-        }
-    }
-    if (bricks >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve: too many bricks");
     AC_CUDA(sc.desc.ensure(sizeof(VolDesc) * n_sets));
-    AC_CUDA(cudaMemcpyAsync(sc.desc.p, desc.data(), sizeof(VolDesc) * n_sets, cudaMemcpyHostToDevice, st));
+    AC_CUDA(cudaMemcpyAsync(sc.desc.p, pr.desc.data(), sizeof(VolDesc) * n_sets, cudaMemcpyHostToDevice, st));
     a.vols = sc.desc.as<VolDesc>();
-
-    ac_contours *owner = sets[0];
-    AC_CUDA(cudaMemsetAsync(owner->path_counts, 0, sizeof(unsigned long long) * 3, st));
-    if (!owner->ev0) {
-        AC_CUDA(cudaEventCreate(&owner->ev0));
-        AC_CUDA(cudaEventCreate(&owner->ev1));
+    if (!sets[0]->ev0) {
+        AC_CUDA(cudaEventCreate(&sets[0]->ev0));
+        AC_CUDA(cudaEventCreate(&sets[0]->ev1));
     }
-    if (!pl.brick) {
-        const int64_t per_cta = (int64_t)pl.warps * 32 / pl.G;
-        const int64_t grid = std::min<int64_t>((total + per_cta - 1) / per_cta, (int64_t)1 << 30);
-        AC_CUDA(cudaEventRecord(owner->ev0, st));
-        for (int n = a.first_iter; n <= a.last_iter; ++n) {
-            a.iter0 = n;
-            cudaError_t e = launch_evolve(v0->dtype, a, pl, grid, st);
-            if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: plain launch: ") + cudaGetErrorString(e));
-            count_launch();
-        }
-        AC_CUDA(cudaEventRecord(owner->ev1, st));
-        owner->timed = true;
-        return AC_OK;
-    }
+    if (!pl.brick) return AC_OK;
 
     // tensor maps: one box of the staged-region size per volume
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) AC_FAIL(AC_ERR_CUDA, "ac_evolve: cuTensorMapEncodeTiled is not available from the driver");
-    std::vector<CUtensorMap> maps(n_sets);
+    pr.maps.assign(n_sets, CUtensorMap());
     for (int i = 0; i < n_sets; ++i) {
         const ac_volume *v = sets[i]->vol;
         cuuint64_t gdim[3] = {(cuuint64_t)v->n[0], (cuuint64_t)v->n[1], (cuuint64_t)v->n[2]};
         cuuint64_t gstride[2] = {(cuuint64_t)(v->pitch_y * v->es), (cuuint64_t)(v->pitch_z * v->es)};
         cuuint32_t box[3] = {(cuuint32_t)pl.ext[0], (cuuint32_t)pl.ext[1], (cuuint32_t)pl.ext[2]};
         cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = enc(&maps[i], tma_type(v->dtype), 3, v->data, gdim, gstride, box, estr,
+        CUresult r = enc(&pr.maps[i], tma_type(v->dtype), 3, v->data, gdim, gstride, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) AC_FAIL(AC_ERR_CUDA, "ac_evolve: cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
     }
     AC_CUDA(sc.tmaps.ensure(sizeof(CUtensorMap) * n_sets + 128));
     CUtensorMap *dmaps = reinterpret_cast<CUtensorMap *>(((uintptr_t)sc.tmaps.p + 127) & ~(uintptr_t)127);
-    AC_CUDA(cudaMemcpyAsync(dmaps, maps.data(), sizeof(CUtensorMap) * n_sets, cudaMemcpyHostToDevice, st));
+    AC_CUDA(cudaMemcpyAsync(dmaps, pr.maps.data(), sizeof(CUtensorMap) * n_sets, cudaMemcpyHostToDevice, st));
 
-    // bin contours by brick (their current centre) and sort by brick
+    // binning and sort space
     AC_CUDA(sc.keys.ensure(sizeof(uint32_t) * total));
     AC_CUDA(sc.vals.ensure(sizeof(uint32_t) * total));
     AC_CUDA(sc.skeys.ensure(sizeof(uint32_t) * total));
     AC_CUDA(sc.svals.ensure(sizeof(uint32_t) * total));
-    {
-        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 1 << 16);
-        bin_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.vols, n_sets, total, make_int3(pl.B[0], pl.B[1], pl.B[2]),
-                                                     sc.keys.as<uint32_t>(), sc.vals.as<uint32_t>());
-        count_launch();
-        AC_CUDA(cudaGetLastError());
-    }
-    int end_bit = 1;
-    while (((int64_t)1 << end_bit) < bricks + 1) ++end_bit;
-    size_t tmp = 0;
-    AC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, sc.keys.as<uint32_t>(), sc.skeys.as<uint32_t>(),
-                                            sc.vals.as<uint32_t>(), sc.svals.as<uint32_t>(), (int)total, 0, end_bit, st));
-    AC_CUDA(sc.cub.ensure(tmp));
-    AC_CUDA(cub::DeviceRadixSort::SortPairs(sc.cub.p, tmp, sc.keys.as<uint32_t>(), sc.skeys.as<uint32_t>(),
-                                            sc.vals.as<uint32_t>(), sc.svals.as<uint32_t>(), (int)total, 0, end_bit, st));
+    pr.end_bit = 1;
+    while (((int64_t)1 << pr.end_bit) < bricks + 1) ++pr.end_bit;
+    AC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, pr.cub_bytes, sc.keys.as<uint32_t>(), sc.skeys.as<uint32_t>(),
+                                            sc.vals.as<uint32_t>(), sc.svals.as<uint32_t>(), (int)total, 0, pr.end_bit, st));
+    AC_CUDA(sc.cub.ensure(pr.cub_bytes));
 
     a.tmaps = dmaps;
     a.sorted_brick = sc.skeys.as<uint32_t>();
@@ -773,13 +785,64 @@ ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int 
     a.raw_bytes = pl.raw;
     a.quad_off = pl.quad_off;
     a.smem_bytes = pl.smem;
-    AC_CUDA(cudaEventRecord(owner->ev0, st));
-    cudaError_t e = launch_evolve(v0->dtype, a, pl, bricks, st);
-    if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: brick launch: ") + cudaGetErrorString(e));
-    count_launch();
-    AC_CUDA(cudaEventRecord(owner->ev1, st));
-    owner->timed = true;
     return AC_OK;
+}
+
+// Device work of a prepared launch only (no host synchronisation, no allocation):
+// counters, binning by brick, sort, evolution kernel(s), kernel-time events.
+// While a stream is captured, the kernel-time events become event-record nodes of
+// the graph (cudaEventRecordExternal), so that each replay records them.
+ac_status enqueue_prepared(Prepared &pr, Scratch &sc, cudaStream_t st, int64_t *launches, bool count = true,
+                           bool capturing = false)
+{
+    if (pr.total == 0) return AC_OK;
+    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    EvolveArgs a = pr.a;
+    ac_contours *owner = pr.owner;
+    int64_t nl = 0;
+    AC_CUDA(cudaMemsetAsync(owner->path_counts, 0, sizeof(unsigned long long) * 3, st));
+    if (!pr.pl.brick) {
+        const int64_t per_cta = (int64_t)pr.pl.warps * 32 / pr.pl.G;
+        const int64_t grid = std::min<int64_t>((pr.total + per_cta - 1) / per_cta, (int64_t)1 << 30);
+        AC_CUDA(cudaEventRecordWithFlags(owner->ev0, st, ev_flags));
+        for (int n = a.first_iter; n <= a.last_iter; ++n) {
+            a.iter0 = n;
+            cudaError_t e = launch_evolve(pr.dtype, a, pr.pl, grid, st);
+            if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: plain launch: ") + cudaGetErrorString(e));
+            ++nl;
+        }
+        AC_CUDA(cudaEventRecordWithFlags(owner->ev1, st, ev_flags));
+    } else {
+        const int64_t blocks = std::min<int64_t>((pr.total + 255) / 256, 1 << 16);
+        bin_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.vols, pr.n_sets, pr.total,
+                                                     make_int3(pr.pl.B[0], pr.pl.B[1], pr.pl.B[2]),
+                                                     sc.keys.as<uint32_t>(), sc.vals.as<uint32_t>());
+        ++nl;
+        AC_CUDA(cudaGetLastError());
+        size_t tmp = pr.cub_bytes;
+        AC_CUDA(cub::DeviceRadixSort::SortPairs(sc.cub.p, tmp, sc.keys.as<uint32_t>(), sc.skeys.as<uint32_t>(),
+                                                sc.vals.as<uint32_t>(), sc.svals.as<uint32_t>(), (int)pr.total, 0,
+                                                pr.end_bit, st));
+        AC_CUDA(cudaEventRecordWithFlags(owner->ev0, st, ev_flags));
+        cudaError_t e = launch_evolve(pr.dtype, a, pr.pl, pr.bricks, st);
+        if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: brick launch: ") + cudaGetErrorString(e));
+        ++nl;
+        AC_CUDA(cudaEventRecordWithFlags(owner->ev1, st, ev_flags));
+    }
+    owner->timed = true;
+    if (launches) *launches = nl;
+    if (count) count_launch(nl);
+    return AC_OK;
+}
+
+// ac_evolve and ac_evolve_batch: sets[0] owns the scratch buffers.
+ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int n_sets, const ac_evolve_params *p,
+                      const ac_trace *trace, cudaStream_t st)
+{
+    Prepared pr;
+    ac_status s = prepare_sets(sets, items, n_sets, p, trace, sets[0]->scratch, pr, st);
+    if (s != AC_OK) return s;
+    return enqueue_prepared(pr, sets[0]->scratch, st, nullptr);
 }
 
 }  // namespace
@@ -1000,6 +1063,254 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
         count_launch();
     }
     return check_status(&ctr, st);
+}
+
+// ------------------------------------------------------------------ plans, graphs, autotuning
+struct ac_plan {
+    std::vector<ac_contours *> sets;
+    ac_evolve_params params;
+    Prepared pr;
+    Scratch sc;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_launches = 0;
+    int32_t span0 = 0, span1 = 0;   // iteration span the graph was captured with
+};
+
+static void drop_graph(ac_plan *pl)
+{
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+}
+
+extern "C" ac_status ac_plan_create(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
+                                    const ac_evolve_params *params, ac_plan **out)
+{
+    g_err.clear();
+    if (!out) AC_FAIL(AC_ERR_ARG, "ac_plan_create: out is NULL");
+    *out = nullptr;
+    if (!sets || n_sets < 1 || n_sets > 4096 || !params) AC_FAIL(AC_ERR_ARG, "ac_plan_create: need 1..4096 sets and params");
+    ac_plan *pl = new ac_plan();
+    pl->sets.assign(sets, sets + n_sets);
+    pl->params = *params;
+    ac_status s = prepare_sets(pl->sets.data(), items, n_sets, params, nullptr, pl->sc, pl->pr, 0);
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (s == AC_OK && e != cudaSuccess) {
+        ac::set_error(std::string("ac_plan_create: ") + cudaGetErrorString(e));
+        s = AC_ERR_CUDA;
+    }
+    if (s != AC_OK) {
+        pl->sc.release_all();
+        delete pl;
+        return s;
+    }
+    *out = pl;
+    return AC_OK;
+}
+
+extern "C" ac_status ac_plan_set_items(ac_plan *pl, const ac_batch_item *items, void *cuda_stream)
+{
+    g_err.clear();
+    if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_set_items: NULL plan");
+    ac_status s = apply_items(pl->pr, items, &pl->params);
+    if (s != AC_OK) return s;
+    if (pl->pr.total == 0) return AC_OK;
+    AC_CUDA(cudaMemcpyAsync(pl->sc.desc.p, pl->pr.desc.data(), sizeof(VolDesc) * pl->pr.n_sets,
+                            cudaMemcpyHostToDevice, (cudaStream_t)cuda_stream));
+    // a captured plain-path graph holds one launch per iteration of its span
+    if (!pl->pr.pl.brick && (pl->pr.a.first_iter != pl->span0 || pl->pr.a.last_iter != pl->span1)) drop_graph(pl);
+    return AC_OK;
+}
+
+extern "C" ac_status ac_plan_launch(ac_plan *pl, int use_graph, void *cuda_stream)
+{
+    g_err.clear();
+    if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_launch: NULL plan");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!use_graph) return enqueue_prepared(pl->pr, pl->sc, st, nullptr);
+    if (!pl->exec) {
+        // capture once on a stream of the plan's own (the legacy stream cannot capture)
+        if (!pl->cap_stream) AC_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+        AC_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
+        int64_t n = 0;
+        ac_status s = enqueue_prepared(pl->pr, pl->sc, pl->cap_stream, &n, false, true);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+        if (s != AC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        AC_CUDA(e);
+        pl->graph = g;
+        AC_CUDA(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+        pl->graph_launches = n;
+        pl->span0 = pl->pr.a.first_iter;
+        pl->span1 = pl->pr.a.last_iter;
+    }
+    AC_CUDA(cudaGraphLaunch(pl->exec, st));
+    count_launch(pl->graph_launches);
+    return AC_OK;
+}
+
+extern "C" void ac_destroy_plan(ac_plan *pl)
+{
+    if (!pl) return;
+    drop_graph(pl);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    pl->sc.release_all();
+    delete pl;
+}
+
+namespace {
+
+struct TuneKey {
+    int ndim, dtype, N, G_in, comp, acc, halo_milli;
+    int64_t stride_milli, r_milli;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(ndim, dtype, N, G_in, comp, acc, halo_milli, stride_milli, r_milli) <
+               std::tie(o.ndim, o.dtype, o.N, o.G_in, o.comp, o.acc, o.halo_milli, o.stride_milli, o.r_milli);
+    }
+};
+struct TuneVal {
+    int G, warps, brick[3];
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+}  // namespace
+
+extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_evolve_params *params, void *cuda_stream)
+{
+    g_err.clear();
+    if (!sets || n_sets < 1 || n_sets > 4096 || !params) AC_FAIL(AC_ERR_ARG, "ac_autotune: need 1..4096 sets and params");
+    ac_status s = check_params(params);
+    if (s != AC_OK) return s;
+    if (params->path != AC_PATH_BRICK) return AC_OK;   // nothing to tune on the plain path
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const ac_volume *v0 = sets[0]->vol;
+    double stride_hint = 0, r_hint = 0;
+    for (int i = 0; i < n_sets; ++i) {
+        if (!sets[i] || !sets[i]->vol) AC_FAIL(AC_ERR_ARG, "ac_autotune: NULL contour set");
+        stride_hint = std::max(stride_hint, sets[i]->stride_hint);
+        r_hint = std::max(r_hint, sets[i]->r_hint);
+    }
+    const bool comp = params->compensated != 0;
+    const bool acc = params->sampling == 1 || (params->sampling == 0 && params->N < 64);
+    const TuneKey key{v0->ndim, (int)v0->dtype, params->N, params->lanes_per_contour, comp, acc,
+                      (int)std::lround(params->halo_factor * 1000), (int64_t)std::llround(stride_hint * 1000),
+                      (int64_t)std::llround(r_hint * 1000)};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            params->lanes_per_contour = it->second.G;
+            params->warps_per_block = it->second.warps;
+            for (int d = 0; d < 3; ++d) params->brick[d] = it->second.brick[d];
+            return AC_OK;
+        }
+    }
+    // candidates: lanes per contour x lattice cells per brick
+    std::vector<int> Gs;
+    for (int G : {4, 8, 16, 32}) {
+        if (params->lanes_per_contour && G != params->lanes_per_contour) continue;
+        if (G == 4 && (!comp || acc)) continue;
+        if (G > 4 && (int64_t)G > params->N) continue;
+        Gs.push_back(G);
+    }
+    std::vector<std::array<int, 3>> cells;
+    if (v0->ndim == 2) cells = {{8, 8, 1}, {12, 8, 1}, {16, 8, 1}, {16, 16, 1}};
+    else cells = {{2, 2, 2}, {2, 2, 1}, {3, 3, 2}, {4, 4, 2}};
+
+    // trial copies of the contour states (trials must not move the real contours)
+    std::vector<ac_contours> tmp(n_sets);
+    std::vector<ac_contours *> tsets(n_sets);
+    std::vector<float *> copies(n_sets, nullptr);
+    int32_t *tstatus = nullptr;
+    unsigned long long *tcounts = nullptr;
+    auto cleanup = [&]() {
+        for (float *c : copies)
+            if (c) cudaFree(c);
+        if (tstatus) cudaFree(tstatus);
+        if (tcounts) cudaFree(tcounts);
+        for (auto &t : tmp) {
+            t.scratch.release_all();
+            if (t.ev0) cudaEventDestroy(t.ev0);
+            if (t.ev1) cudaEventDestroy(t.ev1);
+        }
+    };
+    cudaError_t e = cudaMalloc(&tstatus, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&tcounts, sizeof(unsigned long long) * 4);
+    for (int i = 0; i < n_sets && e == cudaSuccess; ++i) {
+        e = cudaMalloc(&copies[i], sizeof(float) * 5 * std::max<int64_t>(1, sets[i]->C));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(copies[i], sets[i]->state, sizeof(float) * 5 * sets[i]->C, cudaMemcpyDeviceToDevice, st);
+        tmp[i].vol = sets[i]->vol;
+        tmp[i].C = sets[i]->C;
+        tmp[i].state = copies[i];
+        tmp[i].status = tstatus;
+        tmp[i].path_counts = tcounts;
+        tmp[i].r_hint = sets[i]->r_hint;
+        tmp[i].stride_hint = sets[i]->stride_hint;
+        tsets[i] = &tmp[i];
+    }
+    if (e != cudaSuccess) {
+        cleanup();
+        AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
+                std::string("ac_autotune: trial state: ") + cudaGetErrorString(e));
+    }
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best_ms = 1e30f;
+    TuneVal best{0, 0, {0, 0, 0}};
+    for (int G : Gs) {
+        for (const auto &cl : cells) {
+            ac_evolve_params tp = *params;
+            tp.lanes_per_contour = G;
+            tp.warps_per_block = 0;
+            tp.T = std::min(params->T, 3);
+            tp.first_iter = 1;
+            tp.update_last = 0;
+            double per = 1.0;
+            for (int d = 0; d < 3; ++d) {
+                tp.brick[d] = d < v0->ndim ? std::max(1, (int)std::lround(cl[d] * stride_hint / v0->sp[d])) : 0;
+                if (d < v0->ndim) per *= cl[d];
+            }
+            if (per * G / 32.0 > 16.0) continue;   // more groups than a CTA holds
+            Prepared pr;
+            if (prepare_sets(tsets.data(), nullptr, n_sets, &tp, nullptr, tmp[0].scratch, pr, st) != AC_OK) continue;
+            if (enqueue_prepared(pr, tmp[0].scratch, st, nullptr, false) != AC_OK) continue;   // warm-up
+            cudaEventRecord(t0, st);
+            if (enqueue_prepared(pr, tmp[0].scratch, st, nullptr, false) != AC_OK) continue;
+            cudaEventRecord(t1, st);
+            if (cudaEventSynchronize(t1) != cudaSuccess) continue;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = TuneVal{G, pr.pl.warps, {tp.brick[0], tp.brick[1], tp.brick[2]}};
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    cleanup();
+    if (best.G == 0) AC_FAIL(AC_ERR_ARG, "ac_autotune: no candidate configuration could run");
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    params->lanes_per_contour = best.G;
+    params->warps_per_block = best.warps;
+    for (int d = 0; d < 3; ++d) params->brick[d] = best.brick[d];
+    return AC_OK;
 }
 
 extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_trace *trace,

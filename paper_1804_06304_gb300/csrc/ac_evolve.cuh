@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
 
     const int v = find_vol(a, b, true);
     const VolDesc &V = a.vols[v];
+    if (V.first_iter > V.last_iter) return;   // no iterations for this set in this launch
     const int64_t lb = b - V.brick_base;
     const int bxi = (int)(lb % V.nb[0]);
     const int byi = (int)((lb / V.nb[0]) % V.nb[1]);
