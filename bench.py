@@ -64,6 +64,12 @@ WORKLOADS = {
                      desc="64 uint8 volumes 64^3..512x512x128 (log-uniform voxel count), 1 nucleus per 2000 voxels, "
                           "r 3-8; stride-4 lattices; one autotuned plan over all volumes replayed as a CUDA graph; "
                           "256 samples, 80 iterations"),
+    "serve-3d": dict(ndim=3, stride=6.0, N=512, T=100, seed=4, tiles=8, requests=32, load=0.7, ipr=10,
+                     budget_gb=120,
+                     desc="request loop over uint16 tiles 128^3..1024x1024x64 (log-uniform voxel count, brain-3d "
+                          "nucleus model, 8 distinct tiles cycled with distinct Philox streams), 32 requests; "
+                          "saturated (all submitted at once) and Poisson arrivals at 0.7x the saturated rate; "
+                          "HBM budget 120 GB, 10 iterations per round; 512 samples, 100 iterations"),
 }
 
 
@@ -72,8 +78,8 @@ def make_input(name: str, seed: int, dtype: str, size: int = 0):
     if name == "large-2d":
         side = size or 4096
         s = synth.large_2d(seed, shape=(side, side), n_nuclei=int(round(12_000 * side * side / 4096**2)))
-    elif name == "batch-3d":
-        raise ValueError("batch-3d has no single input")
+    elif name in ("batch-3d", "serve-3d"):
+        raise ValueError(f"{name} has no single input")
     elif name == "brain-3d":
         side = size or 1024
         s = synth.brain_3d(seed, shape=(side, side, side // 4), n_nuclei=int(round(100_000 * (side / 1024) ** 3)),
@@ -257,6 +263,8 @@ def main(argv=None):
     dev = torch.device("cuda", local)
     if args.workload == "batch-3d":
         return batch_arm(args, wl, rank, world, dev)
+    if args.workload == "serve-3d":
+        return serve_arm(args, wl, rank, world, dev)
 
     s, vol = make_input(args.workload, wl["seed"] + rank, args.dtype, args.size)
     spacing = s.spacing
@@ -481,15 +489,123 @@ def batch_arm(args, wl, rank, world, dev):
         dist.destroy_process_group()
 
 
+def serve_arm(args, wl, rank, world, dev):
+    """Serving form: tiles submitted to the library's request loop (ac_server_*),
+    first all at once (saturated throughput), then as Poisson arrivals at a fraction
+    of that rate (tile latency p50 / p99, host clock from submit to cells ready).
+    Tiles come from pinned host memory, so every request includes its upload."""
+    import torch
+    import torch.distributed as dist
+    from paper_1804_06304_gb300 import ac, synth
+
+    dist_on = world > 1
+    tiles = [t for _, t in synth.tile_stream(wl["seed"] + rank, count=wl["tiles"])]
+    pinned = [torch.from_numpy(t.volume).pin_memory().numpy() for t in tiles]
+    R0 = wl["stride"] / math.sqrt(1.5)
+    contrast = tiles[0].contrast
+    params = ac.default_params(3, R0, contrast, N=wl["N"], T=wl["T"], seed=2000 + rank,
+                               compensated=args.compensated)
+    # brick shape and lane grouping tuned once on two tiles of the stream
+    probe = [ac.ac_seed(ac.ac_create_volume(pinned[i], tiles[i].spacing), stride=wl["stride"]) for i in (0, 1)]
+    params = ac.ac_autotune(probe, params)
+    del probe
+    E0 = ac.default_E0(3, contrast)
+    n_req = wl["requests"]
+
+    def contours(t):
+        return int(np.prod([max(1, int(math.floor(n * sp / wl["stride"]))) for n, sp in
+                            zip(t.shape_xyz, t.spacing)]))
+
+    def run(arrivals):
+        srv = ac.Server(params, ac.AC_U16, 3, wl["stride"], E0, hbm_budget_bytes=int(wl["budget_gb"] * 1e9),
+                        iters_per_round=wl["ipr"])
+        t0 = time.perf_counter()
+        tickets = []
+        for i, a in enumerate(arrivals):
+            delay = t0 + a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            j = i % len(tiles)
+            tickets.append((j, srv.submit(pinned[j], tiles[j].spacing, stream_id=i)))
+        res = [srv.wait(tk, timeout=600)[1] for _, tk in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        samples = sum(contours(tiles[j]) for j, _ in tickets) * wl["N"] * wl["T"]
+        voxels = sum(tiles[j].volume.size for j, _ in tickets)
+        return wall, samples, voxels, res, st
+
+    run([0.0] * max(args.warmup, 1))                      # warm-up requests
+    torch.cuda.synchronize()
+    if dist_on:
+        dist.barrier()
+    clocks = ClockSampler(None)
+    clocks.start()
+    launches0 = ac.ac_kernel_launches()
+    wall, samples, voxels, res_sat, st_sat = run([0.0] * n_req)
+    launches = ac.ac_kernel_launches() - launches0
+    rate = n_req / wall
+    lam = wl["load"] * rate
+    rng = np.random.default_rng(wl["seed"])
+    arrivals = list(np.cumsum(rng.exponential(1.0 / lam, size=n_req)) - 0.0)
+    arrivals = [a - arrivals[0] for a in arrivals]
+    wall_p, samples_p, voxels_p, res_p, st_p = run(arrivals)
+    clk = clocks.stop()
+    reducer = torch_max_reducer(dev) if dist_on else None
+    t_ms, value = aggregate_ranks([wall * 1e3], samples, world, reducer)
+    lat = np.array([r["total_ms"] for r in res_p])
+    lat_sat = np.array([r["total_ms"] for r in res_sat])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, thr, desc = oracle_sample_batch(tiles, wl, args.cpu_seconds)
+        cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc}
+    achieved = ALG_SLOTS_PER_SAMPLE[3] * samples / wall / 1e12
+    peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "MC contour samples/s (serving form: upload, seed, evolve, localize per tile)",
+            "value": value, "unit": "samples/s", "n_gpus": world, "steps": n_req, "warmup": max(args.warmup, 1),
+            "ms_per_step": t_ms / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 arithmetic on uint16 voxels", "data": "synthetic",
+            "config": {"workload": "serve-3d", "desc": wl["desc"], "requests": n_req,
+                       "autotuned": {"lanes_per_contour": params.lanes_per_contour, "brick": list(params.brick),
+                                     "warps_per_block": params.warps_per_block},
+                       "timing": "host clock around the request loop (submit to the last cells)",
+                       "l2": "inputs larger than L2 in total; each request uploads its tile",
+                       "parallelism": f"replicas x{world}"},
+            "voxels_per_s": voxels / wall,
+            "serving": {"saturated_tiles_per_s": rate, "saturated_latency_ms_p50": float(np.median(lat_sat)),
+                        "poisson_lambda_hz": lam, "poisson_tiles_per_s": n_req / wall_p,
+                        "poisson_voxels_per_s": voxels_p / wall_p, "poisson_samples_per_s": samples_p / wall_p,
+                        "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                        "queue_ms_p50": float(np.median([r["queue_ms"] for r in res_p])),
+                        "rounds_saturated": st_sat["rounds"], "rounds_poisson": st_p["rounds"],
+                        "peak_resident_gb": st_sat["peak_resident_bytes"] / 1e9},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "whole request loop (host clock; uploads, seeding and localization included)",
+                         "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[3]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "samples/s", "ms_per_step": t_ms / n_req,
+                    "h2d_bytes_per_step": int(voxels * 2 / n_req),
+                    "d2h_bytes_per_step": int(sum(r["n_cells"] for r in res_sat) * 24 / n_req),
+                    "note": "the serving value is end to end: host tiles in, cells out"},
+            "clocks": clk}))
+    if dist_on:
+        dist.destroy_process_group()
+
+
 def reference_arm(args, wl, rank, world):
     """The FP64 oracle timed on the host cores: each step a bounded random sample of
     the same workload's contours (all iterations)."""
     if rank != 0:
         return
     per_step = max(2.0, min(15.0, 120.0 / max(1, args.steps + args.warmup)))
-    if args.workload == "batch-3d":
+    if args.workload in ("batch-3d", "serve-3d"):
         from paper_1804_06304_gb300 import synth
-        vols = synth.batch_3d(wl["seed"], count=wl["count"])
+        vols = synth.batch_3d(wl["seed"], count=wl["count"]) if args.workload == "batch-3d" else \
+            [t for _, t in synth.tile_stream(wl["seed"], count=wl["tiles"])]
         run = lambda seed: oracle_sample_batch(vols, wl, per_step, rng_seed=seed)  # noqa: E731
         C = sum(lattice_count(sv.shape_xyz, sv.spacing, wl["stride"], 3) for sv in vols)
     else:

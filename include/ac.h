@@ -182,6 +182,8 @@ ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_t
  * so it gives exactly what ac_evolve on that set alone gives with those values.
  * items NULL: every set uses params' stream_id, first_iter, T and update_last.
  * A set with n_iter = 0 is left untouched.  Every set must share dtype and ndim.
+ * Each set keeps its own status word: a non-finite state or a wait that gave up is
+ * reported by the calls on the set where it happened (ac_get_state, ac_localize).
  * Asynchronous.  Errors as ac_evolve.
  */
 typedef struct {
@@ -202,13 +204,20 @@ ac_status ac_evolve_batch(ac_contours *const *sets, const ac_batch_item *items, 
  * with use_graph = 1 that sequence is captured once into a CUDA graph and replayed
  * on every later launch.  ac_plan_set_items changes the sets' iteration windows
  * and stream words for later launches (a plain-path graph is recaptured when the
- * iteration span changes).  The sets, their volumes and the plan's own buffers
- * must stay alive and unmoved while the plan exists; launches on one plan are
- * serialised by the caller's stream.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ * iteration span changes).  ac_plan_rebind replaces the plan's sets (and their
+ * items) for later launches, keeping the plan's parameters and reusing its device
+ * buffers, which only grow; it drops the captured graph, uploads on the stream and
+ * does not synchronize.  After a failed rebind the plan has no sets and its
+ * launches return AC_ERR_STATE until a rebind succeeds.  The sets, their volumes
+ * and the plan's own buffers must stay alive and unmoved while the plan launches
+ * on them; launches on one plan are serialised by the caller's stream.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STATE.
  */
 typedef struct ac_plan ac_plan;
 ac_status ac_plan_create(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
                          const ac_evolve_params *params, ac_plan **out);
+ac_status ac_plan_rebind(ac_plan *plan, ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
+                         void *cuda_stream);
 ac_status ac_plan_set_items(ac_plan *plan, const ac_batch_item *items, void *cuda_stream);
 ac_status ac_plan_launch(ac_plan *plan, int use_graph, void *cuda_stream);
 void ac_destroy_plan(ac_plan *plan);

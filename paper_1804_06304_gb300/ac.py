@@ -63,6 +63,24 @@ class ac_cell(ct.Structure):
 
 CELL_DTYPE = np.dtype([("c", np.float32, 3), ("r", np.float32), ("E", np.float32), ("id", np.int32)])
 
+
+class ac_server_params(ct.Structure):
+    _fields_ = [("evolve", ac_evolve_params), ("dtype", ct.c_int32), ("ndim", ct.c_int32), ("stride", ct.c_float),
+                ("R0", ct.c_float), ("E0", ct.c_float), ("iters_per_round", ct.c_int32),
+                ("max_resident", ct.c_int32), ("hbm_budget_bytes", ct.c_int64)]
+
+
+class ac_tile_result(ct.Structure):
+    _fields_ = [("ticket", ct.c_int64), ("status", ct.c_int32), ("rounds", ct.c_int32), ("n_cells", ct.c_int64),
+                ("contours", ct.c_int64), ("voxels", ct.c_int64), ("est_bytes", ct.c_int64),
+                ("queue_ms", ct.c_double), ("run_ms", ct.c_double), ("total_ms", ct.c_double)]
+
+
+class ac_server_stats(ct.Structure):
+    _fields_ = [("pending", ct.c_int64), ("resident", ct.c_int64), ("finished", ct.c_int64),
+                ("completed", ct.c_int64), ("failed", ct.c_int64), ("rounds", ct.c_int64),
+                ("resident_bytes", ct.c_int64), ("peak_resident_bytes", ct.c_int64), ("budget_bytes", ct.c_int64)]
+
 _SIGS = {
     "ac_create_volume": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_int64), ct.c_int64,
                                     ct.c_int64, ct.POINTER(ct.c_float), ct.c_float, ct.c_void_p,
@@ -91,11 +109,20 @@ _SIGS = {
                                     ct.c_float, ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_plan_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ac_batch_item), ct.c_int32,
                                   ct.POINTER(ac_evolve_params), ct.POINTER(ct.c_void_p)]),
+    "ac_plan_rebind": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(ac_batch_item), ct.c_int32,
+                                  ct.c_void_p]),
     "ac_plan_set_items": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_batch_item), ct.c_void_p]),
     "ac_plan_launch": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p]),
     "ac_destroy_plan": (None, [ct.c_void_p]),
     "ac_autotune": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int32, ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_last_error": (ct.c_char_p, []),
+    "ac_server_create": (ct.c_int, [ct.POINTER(ac_server_params), ct.POINTER(ct.c_void_p)]),
+    "ac_server_submit": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
+                                    ct.POINTER(ct.c_float), ct.c_float, ct.c_uint32, ct.POINTER(ct.c_int64)]),
+    "ac_server_wait": (ct.c_int, [ct.c_void_p, ct.c_int64, ct.c_double, ct.c_void_p, ct.c_int64,
+                                  ct.POINTER(ac_tile_result)]),
+    "ac_server_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_server_stats)]),
+    "ac_server_destroy": (None, [ct.c_void_p]),
 }
 
 _lib = None
@@ -120,8 +147,9 @@ def load():
 
 
 def header_symbols() -> list:
-    """Entry points declared in include/ac.h."""
-    h = open(os.path.join(os.path.dirname(_build.HERE), "include", "ac.h")).read()
+    """Entry points declared in include/*.h."""
+    inc = os.path.join(os.path.dirname(_build.HERE), "include")
+    h = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"\b(ac_[a-z0-9_]+)\s*\(", h)))
 
 
@@ -351,6 +379,13 @@ def ac_plan_create(sets, params: EvolveParams, items=None) -> Plan:
     return Plan(out, sets)
 
 
+def ac_plan_rebind(plan: Plan, sets, items=None, stream=None):
+    """New contour sets (and items) for later launches of the plan."""
+    _check(load().ac_plan_rebind(plan.handle, _handles(sets), _items(items, len(sets)), len(sets),
+                                 ct.c_void_p(_stream(stream))))
+    plan.sets = list(sets)
+
+
 def ac_plan_set_items(plan: Plan, items, stream=None):
     _check(load().ac_plan_set_items(plan.handle, _items(items, len(plan.sets)), ct.c_void_p(_stream(stream))))
 
@@ -455,3 +490,75 @@ def ac_evolve_static(volume_dev, state_dev, params: EvolveParams, r0: float, str
 
 def ac_last_error() -> str:
     return load().ac_last_error().decode()
+
+
+# ------------------------------------------------------------------------ serving form
+class Server:
+    """Request loop over image tiles (include/ac_serve.h).  ``submit`` keeps a
+    reference to each tile's array until its ticket is collected by ``wait``."""
+
+    def __init__(self, params: EvolveParams, dtype: int, ndim: int, stride: float, E0: float,
+                 hbm_budget_bytes: int, iters_per_round: int = 10, max_resident: int = 0, R0: float = 0.0):
+        sp = ac_server_params()
+        sp.evolve = params.to_c()
+        sp.dtype, sp.ndim, sp.stride, sp.R0, sp.E0 = int(dtype), int(ndim), float(stride), float(R0), float(E0)
+        sp.iters_per_round, sp.max_resident, sp.hbm_budget_bytes = int(iters_per_round), int(max_resident), \
+            int(hbm_budget_bytes)
+        self.handle = None
+        out = ct.c_void_p()
+        _check(load().ac_server_create(ct.byref(sp), ct.byref(out)))
+        self.handle = out
+        self._arrays = {}
+        self._caps = {}
+        self.ndim, self.stride = int(ndim), float(stride)
+
+    def submit(self, volume: np.ndarray, spacing=(1.0, 1.0, 1.0), intensity_scale: float = 1.0,
+               stream_id: int = 0) -> int:
+        """``volume`` indexed [z, y, x] (3D) or [y, x] (2D), host memory, x fastest."""
+        a = np.asarray(volume)
+        ptr, _, _, shape, strides = _ptr(a)
+        if strides[-1] != 1 or len(shape) not in (2, 3):
+            raise ACError(AC_ERR_ARG, "need a 2D or 3D host array with unit x stride")
+        dims = (ct.c_int64 * 3)(*(list(shape[::-1]) + [1] * (3 - len(shape))))
+        sp = (ct.c_float * 3)(*[float(s) for s in (list(spacing) + [1.0] * 3)[:3]])
+        t = ct.c_int64()
+        _check(load().ac_server_submit(self.handle, ct.c_void_p(ptr), dims, strides[-2],
+                                       strides[-3] if len(shape) == 3 else 0, sp, float(intensity_scale),
+                                       int(stream_id), ct.byref(t)))
+        self._arrays[t.value] = a
+        lattice = 1
+        for d in range(self.ndim):   # ac_seed's lattice size bounds the number of cells
+            lattice *= max(1, int(math.floor(dims[d] * sp[d] / self.stride)))
+        self._caps[t.value] = lattice
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0, cap: int | None = None):
+        """(cells, result dict) of a finished tile; raises ACError on the tile's
+        error or (AC_ERR_TIMEOUT) when it is not finished within ``timeout`` s."""
+        r = ac_tile_result()
+        cap = self._caps.get(ticket, 1) if cap is None else cap
+        out = np.zeros(max(cap, 1), dtype=CELL_DTYPE)
+        st = load().ac_server_wait(self.handle, int(ticket), float(timeout), ct.c_void_p(out.ctypes.data), cap,
+                                   ct.byref(r))
+        if st != AC_ERR_TIMEOUT:
+            self._arrays.pop(ticket, None)
+            self._caps.pop(ticket, None)
+        _check(st)
+        res = {f: getattr(r, f) for f, _ in ac_tile_result._fields_}
+        return out[:min(cap, r.n_cells)].copy(), res
+
+    def stats(self) -> dict:
+        s = ac_server_stats()
+        _check(load().ac_server_get_stats(self.handle, ct.byref(s)))
+        return {f: int(getattr(s, f)) for f, _ in ac_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().ac_server_destroy(self.handle)
+            self.handle = None
+            self._arrays.clear()
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ac_server_destroy(self.handle)
+            self.handle = None

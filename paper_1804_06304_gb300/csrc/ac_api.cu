@@ -32,21 +32,6 @@ void Scratch::release_all()
 
 }  // namespace ac
 
-#define AC_FAIL(code, msg)        \
-    do {                          \
-        ac::set_error(msg);       \
-        return code;              \
-    } while (0)
-
-#define AC_CUDA(call)                                                                                   \
-    do {                                                                                                \
-        cudaError_t e_ = (call);                                                                        \
-        if (e_ != cudaSuccess) {                                                                        \
-            ac::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                          \
-            return e_ == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;                          \
-        }                                                                                               \
-    } while (0)
-
 using namespace ac;
 
 static int elem_size(ac_dtype t)
@@ -578,6 +563,7 @@ VolDesc make_desc(const ac_contours *c, uint32_t stream)
     }
     d.scale = v->scale;
     d.state = c->state;
+    d.status = c->status;
     d.C = c->C;
     d.stream = stream;
     return d;
@@ -698,7 +684,6 @@ ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int
         a.kr2 = (float)(1.0 / dR);
         a.vol_coef = (float)((d == 3 ? 4.0 / 3.0 * M_PI : M_PI) / p->N);
     }
-    a.status = sets[0]->status;
     a.path_counts = sets[0]->path_counts;
 
     pr.desc.assign(n_sets, VolDesc());
@@ -847,6 +832,9 @@ ac_status evolve_sets(ac_contours *const *sets, const ac_batch_item *items, int 
 
 }  // namespace
 
+ac_status ac::check_evolve_params(const ac_evolve_params *p) { return check_params(p); }
+
+
 // ------------------------------------------------------------------ allocation-free evolve
 // One file-scope device array holds every temporary of ac_evolve_static.  Byte
 // layout: [0, 16) status word, [64, 96) path counters, [256, ...) volume
@@ -984,7 +972,6 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
         a.kr2 = (float)(1.0 / dR);
         a.vol_coef = (float)((ndim == 3 ? 4.0 / 3.0 * M_PI : M_PI) / p->N);
     }
-    a.status = ctr.status;
     a.path_counts = ctr.path_counts;
 
     VolDesc desc = make_desc(&ctr, p->stream_id);
@@ -1076,6 +1063,7 @@ struct ac_plan {
     cudaGraphExec_t exec = nullptr;
     int64_t graph_launches = 0;
     int32_t span0 = 0, span1 = 0;   // iteration span the graph was captured with
+    bool valid = true;              // false after a failed rebind
 };
 
 static void drop_graph(ac_plan *pl)
@@ -1111,10 +1099,29 @@ extern "C" ac_status ac_plan_create(ac_contours *const *sets, const ac_batch_ite
     return AC_OK;
 }
 
+extern "C" ac_status ac_plan_rebind(ac_plan *pl, ac_contours *const *sets, const ac_batch_item *items,
+                                    int32_t n_sets, void *cuda_stream)
+{
+    g_err.clear();
+    if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_rebind: NULL plan");
+    if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_plan_rebind: need 1..4096 sets");
+    drop_graph(pl);
+    pl->valid = false;
+    std::vector<ac_contours *> keep(sets, sets + n_sets);
+    Prepared pr;
+    ac_status s = prepare_sets(keep.data(), items, n_sets, &pl->params, nullptr, pl->sc, pr, (cudaStream_t)cuda_stream);
+    if (s != AC_OK) return s;
+    pl->sets = std::move(keep);
+    pl->pr = std::move(pr);
+    pl->valid = true;
+    return AC_OK;
+}
+
 extern "C" ac_status ac_plan_set_items(ac_plan *pl, const ac_batch_item *items, void *cuda_stream)
 {
     g_err.clear();
     if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_set_items: NULL plan");
+    if (!pl->valid) AC_FAIL(AC_ERR_STATE, "ac_plan_set_items: the plan has no sets (a rebind failed)");
     ac_status s = apply_items(pl->pr, items, &pl->params);
     if (s != AC_OK) return s;
     if (pl->pr.total == 0) return AC_OK;
@@ -1129,6 +1136,7 @@ extern "C" ac_status ac_plan_launch(ac_plan *pl, int use_graph, void *cuda_strea
 {
     g_err.clear();
     if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_launch: NULL plan");
+    if (!pl->valid) AC_FAIL(AC_ERR_STATE, "ac_plan_launch: the plan has no sets (a rebind failed)");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!use_graph) return enqueue_prepared(pl->pr, pl->sc, st, nullptr);
     if (!pl->exec) {

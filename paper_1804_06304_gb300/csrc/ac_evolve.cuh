@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
         tma_load_3d(smem_raw, &a.tmaps[v], r0[0], r0[1], r0[2], &mbar);
     }
     if (!mbar_wait_bounded(&mbar, 0, 1u << 22)) {
-        if (threadIdx.x == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
+        if (threadIdx.x == 0) atomicOr(V.status, STATUS_TMA_TIMEOUT);
         mbar_wait_bounded(&mbar, 0, 1u << 22);   // let an in-flight copy land before exit
         return;
     }
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
             }
             if (lig == 0) write_trace(a, v, k, n, c, R, s);
             if (!finite_step(s)) {
-                if (lig == 0) atomicOr(a.status, STATUS_NONFINITE);
+                if (lig == 0) atomicOr(V.status, STATUS_NONFINITE);
                 break;
             }
             if (n < V.last_iter || V.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
             V.state[3 * C + k] = R;
             V.state[4 * C + k] = s.E;
             if (!(isfinite(s.E) && isfinite(R) && isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2])))
-                atomicOr(a.status, STATUS_NONFINITE);
+                atomicOr(V.status, STATUS_NONFINITE);
         }
     }
     // one atomic per warp and path: sum the groups' counts over the warp
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
         if (lig == 0) {
             ++glob;
             write_trace(a, v, k, n, c, R, s);
-            if (!finite_step(s)) atomicOr(a.status, STATUS_NONFINITE);
+            if (!finite_step(s)) atomicOr(V.status, STATUS_NONFINITE);
             else if (n < V.last_iter || V.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
             V.state[k] = c[0];
             V.state[C + k] = c[1];
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
             V.state[3 * C + k] = R;
             V.state[4 * C + k] = s.E;
             if (!(isfinite(s.E) && isfinite(R)))
-                atomicOr(a.status, STATUS_NONFINITE);
+                atomicOr(V.status, STATUS_NONFINITE);
         }
     }
     const unsigned int tot = __reduce_add_sync(0xffffffffu, glob);

@@ -90,8 +90,27 @@ cudaError_t launch_evolve_f16(const EvolveArgs &a, bool brick, int G, bool comp,
 cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                               cudaStream_t st);
 
+// the argument checks of ac_evolve (ac_api.cu)
+ac_status check_evolve_params(const ac_evolve_params *p);
+
 // localization (ac_localize.cu); returns an ac_status and sets the message
 ac_status localize_impl(ac_contours *ctr, float E0, ac_cell *out_host, int64_t cap, int64_t *n_out,
                         cudaStream_t st);
 
 }  // namespace ac
+
+// Error returns of the C ABI entry points: set the calling thread's message.
+#define AC_FAIL(code, msg)        \
+    do {                          \
+        ac::set_error(msg);       \
+        return code;              \
+    } while (0)
+
+#define AC_CUDA(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            ac::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+            return e_ == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;                          \
+        }                                                                                               \
+    } while (0)

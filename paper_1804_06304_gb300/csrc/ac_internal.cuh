@@ -31,6 +31,7 @@ struct VolDesc {
     float scale;         // intensity scale
     int32_t nb[3];       // bricks per axis (brick path)
     float *state;        // 5 x C float32, SoA: cx, cy, cz, R, E
+    int32_t *status;     // this set's sticky status word
     int64_t C;           // contours in this set
     int64_t brick_base;  // first global brick index of this set
     int64_t contour_base;// first global contour index of this set
@@ -72,7 +73,6 @@ struct EvolveArgs {
     float *trace;        // optional (volume 0 only)
     int64_t tk0, tk1;
     int32_t tt0, tt1;
-    int32_t *status;
     unsigned long long *path_counts;   // [3]: fast, clamped, global contour-iterations
 };
 

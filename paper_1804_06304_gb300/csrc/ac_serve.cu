@@ -1,0 +1,384 @@
+// ac_serve.cu -- serving form: a request loop over image tiles on a native worker
+// thread.  The loop is a client of the library's own C ABI (volumes, lattice
+// seeding, a plan over the resident tiles with per-tile iteration windows, and
+// localization), so a tile evolves exactly as it would alone: the sample
+// counters are (j, n, k, stream_id) under the server's single Philox key, and the
+// lane grouping depends only on the evolve parameters, never on the mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ac_host.h"
+#include "ac_serve.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Tile {
+    int64_t ticket = 0;
+    const void *data = nullptr;
+    int64_t dims[3] = {1, 1, 1};
+    int64_t row_stride = 0, plane_stride = 0;
+    float spacing[3] = {1, 1, 1};
+    float scale = 1.0f;
+    uint32_t stream_id = 0;
+    int64_t contours = 0, voxels = 0, est_bytes = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    ac_volume *vol = nullptr;
+    ac_contours *ctr = nullptr;
+    int32_t progress = 0;   // iterations done
+    int32_t rounds = 0;
+    ac_status status = AC_OK;
+    std::string error;
+    std::vector<ac_cell> cells;
+    int64_t n_cells = 0;
+    bool done = false;
+};
+
+int elem_bytes(int dtype) { return dtype == AC_U8 ? 1 : dtype == AC_F32 ? 4 : 2; }
+
+// Lattice size of ac_seed for this tile (cells of side `stride` per axis).
+int64_t lattice_contours(const int64_t dims[3], const float sp[3], int ndim, double stride)
+{
+    int64_t C = 1;
+    for (int d = 0; d < ndim; ++d) C *= std::max<int64_t>(1, (int64_t)std::floor((double)dims[d] * sp[d] / stride));
+    return C;
+}
+
+}  // namespace
+
+struct ac_server {
+    ac_server_params p;
+    int device = 0;
+    cudaStream_t st = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Tile *> pending;
+    std::vector<Tile *> resident;          // changed by the worker only, under mu
+    std::map<int64_t, Tile *> tiles;       // every ticket not yet collected
+    int64_t next_ticket = 1;
+    bool stop = false;
+    int64_t resident_bytes = 0, peak_bytes = 0, rounds = 0, completed = 0, failed = 0, finished = 0;
+    ac_plan *plan = nullptr;               // worker only
+};
+
+namespace {
+
+void release_device(Tile *t)
+{
+    if (t->ctr) ac_destroy_contours(t->ctr);
+    if (t->vol) ac_destroy_volume(t->vol);
+    t->ctr = nullptr;
+    t->vol = nullptr;
+}
+
+// Marks a tile finished (caller holds mu).
+void finish_locked(ac_server *S, Tile *t, ac_status s, const std::string &err)
+{
+    t->status = s;
+    t->error = err;
+    t->t_done = Clock::now();
+    t->done = true;
+    ++S->finished;
+    if (s == AC_OK) ++S->completed;
+    else ++S->failed;
+}
+
+std::string last_error(const char *what)
+{
+    std::string m = ac_last_error();
+    return std::string(what) + (m.empty() ? "" : ": " + m);
+}
+
+void serve_loop(ac_server *S)
+{
+    cudaSetDevice(S->device);
+    const int T = S->p.evolve.T;
+    bool dirty = true;   // the resident set changed since the plan was bound
+    for (;;) {
+        std::vector<Tile *> admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->resident.empty(); });
+            if (S->stop) return;
+            // arrival order, within the budget and the resident cap
+            while (!S->pending.empty()) {
+                Tile *t = S->pending.front();
+                const int64_t n_res = (int64_t)(S->resident.size() + admit.size());
+                if (n_res > 0 && S->resident_bytes + t->est_bytes > S->p.hbm_budget_bytes) break;
+                if (S->p.max_resident > 0 && n_res >= S->p.max_resident) break;
+                S->pending.pop_front();
+                S->resident_bytes += t->est_bytes;
+                S->peak_bytes = std::max(S->peak_bytes, S->resident_bytes);
+                admit.push_back(t);
+            }
+        }
+        // upload and seed outside the lock
+        for (Tile *t : admit) {
+            t->t_admit = Clock::now();
+            ac_status s = ac_create_volume(t->data, 0, (ac_dtype)S->p.dtype, S->p.ndim, t->dims, t->row_stride,
+                                           t->plane_stride, t->spacing, t->scale, S->st, &t->vol);
+            std::string err;
+            if (s != AC_OK) err = last_error("upload");
+            if (s == AC_OK) {
+                ac_seed_params sp{S->p.stride, S->p.R0};
+                s = ac_seed(t->vol, &sp, nullptr, 0, S->st, &t->ctr);
+                if (s != AC_OK) err = last_error("seed");
+            }
+            if (s == AC_OK) t->contours = ac_contour_count(t->ctr);
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (s != AC_OK) {
+                release_device(t);
+                S->resident_bytes -= t->est_bytes;
+                finish_locked(S, t, s, err);
+                S->cv_done.notify_all();
+            } else {
+                S->resident.push_back(t);
+                dirty = true;
+            }
+        }
+        if (S->resident.empty()) continue;
+
+        // one round: every resident tile advances up to iters_per_round iterations
+        const int n = (int)S->resident.size();
+        std::vector<ac_contours *> sets(n);
+        std::vector<ac_batch_item> items(n);
+        for (int i = 0; i < n; ++i) {
+            Tile *t = S->resident[i];
+            const int m = std::min(S->p.iters_per_round, T - t->progress);
+            sets[i] = t->ctr;
+            items[i].stream_id = t->stream_id;
+            items[i].first_iter = t->progress + 1;
+            items[i].n_iter = m;
+            items[i].update_last = t->progress + m < T ? 1 : 0;
+        }
+        ac_status s = AC_OK;
+        const bool rebound = dirty;
+        if (!S->plan) s = ac_plan_create(sets.data(), items.data(), n, &S->p.evolve, &S->plan);
+        else if (dirty) s = ac_plan_rebind(S->plan, sets.data(), items.data(), n, S->st);
+        else s = ac_plan_set_items(S->plan, items.data(), S->st);
+        if (s == AC_OK) s = ac_plan_launch(S->plan, rebound ? 0 : 1, S->st);
+        if (s != AC_OK) {
+            // the launch failed for the whole mix: end every resident tile with it
+            const std::string err = last_error("round");
+            cudaStreamSynchronize(S->st);
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Tile *t : S->resident) {
+                release_device(t);
+                S->resident_bytes -= t->est_bytes;
+                finish_locked(S, t, s, err);
+            }
+            S->resident.clear();
+            if (S->plan) ac_destroy_plan(S->plan);
+            S->plan = nullptr;
+            dirty = true;
+            S->cv_done.notify_all();
+            continue;
+        }
+        dirty = false;
+        for (int i = 0; i < n; ++i) {
+            S->resident[i]->progress += items[i].n_iter;
+            S->resident[i]->rounds += 1;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            ++S->rounds;
+        }
+
+        // retire finished tiles: localize (synchronizes the stream), keep the cells
+        std::vector<Tile *> keep;
+        std::vector<Tile *> done;
+        for (Tile *t : S->resident) (t->progress >= T ? done : keep).push_back(t);
+        if (done.empty()) continue;
+        std::vector<std::pair<ac_status, std::string>> outcome;
+        for (Tile *t : done) {
+            t->cells.resize((size_t)std::max<int64_t>(1, t->contours));
+            int64_t n_out = 0;
+            ac_localize_params lp{S->p.E0};
+            ac_status ls = ac_localize(t->ctr, &lp, t->cells.data(), (int64_t)t->cells.size(), &n_out, S->st);
+            outcome.emplace_back(ls, ls == AC_OK ? std::string() : last_error("localize"));
+            t->n_cells = ls == AC_OK ? n_out : 0;
+            t->cells.resize((size_t)std::min<int64_t>(t->n_cells, (int64_t)t->cells.size()));
+            t->cells.shrink_to_fit();
+        }
+        // the plan still refers to the finished sets: rebind before the next launch
+        dirty = true;
+        for (Tile *t : done) release_device(t);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->resident = keep;
+        for (size_t i = 0; i < done.size(); ++i) {
+            S->resident_bytes -= done[i]->est_bytes;
+            finish_locked(S, done[i], outcome[i].first, outcome[i].second);
+        }
+        S->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" ac_status ac_server_create(const ac_server_params *params, ac_server **out)
+{
+    if (!out) AC_FAIL(AC_ERR_ARG, "ac_server_create: out is NULL");
+    *out = nullptr;
+    if (!params) AC_FAIL(AC_ERR_ARG, "ac_server_create: params is NULL");
+    const ac_server_params &p = *params;
+    if (p.dtype < AC_U8 || p.dtype > AC_F32) AC_FAIL(AC_ERR_ARG, "ac_server_create: unknown dtype");
+    if (p.ndim != 2 && p.ndim != 3) AC_FAIL(AC_ERR_ARG, "ac_server_create: ndim must be 2 or 3");
+    if (!(p.stride > 0.0f) || !std::isfinite(p.stride)) AC_FAIL(AC_ERR_ARG, "ac_server_create: stride must be positive");
+    if (!(p.R0 >= 0.0f) || !std::isfinite(p.R0)) AC_FAIL(AC_ERR_ARG, "ac_server_create: R0 must be >= 0");
+    if (!std::isfinite(p.E0)) AC_FAIL(AC_ERR_ARG, "ac_server_create: E0 must be finite");
+    if (p.iters_per_round < 1) AC_FAIL(AC_ERR_ARG, "ac_server_create: iters_per_round must be >= 1");
+    if (p.max_resident < 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: max_resident must be >= 0");
+    if (p.hbm_budget_bytes <= 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: hbm_budget_bytes must be positive");
+    ac_status s = ac::check_evolve_params(&p.evolve);
+    if (s != AC_OK) return s;
+    ac_server *S = new ac_server();
+    S->p = p;
+    S->p.evolve.first_iter = 0;
+    S->p.evolve.update_last = 0;
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete S;
+        AC_FAIL(AC_ERR_CUDA, std::string("ac_server_create: ") + cudaGetErrorString(e));
+    }
+    S->worker = std::thread(serve_loop, S);
+    *out = S;
+    return AC_OK;
+}
+
+extern "C" ac_status ac_server_submit(ac_server *S, const void *data_host, const int64_t dims[3], int64_t row_stride,
+                                      int64_t plane_stride, const float spacing[3], float intensity_scale,
+                                      uint32_t stream_id, int64_t *ticket)
+{
+    if (!S || !data_host || !dims || !spacing || !ticket) AC_FAIL(AC_ERR_ARG, "ac_server_submit: NULL argument");
+    *ticket = 0;
+    const int nd = S->p.ndim;
+    for (int d = 0; d < 3; ++d) {
+        const int64_t want_min = d < nd ? 2 : 1;
+        if (dims[d] < want_min || dims[d] > ((int64_t)1 << 24) || (d >= nd && dims[d] != 1))
+            AC_FAIL(AC_ERR_ARG, "ac_server_submit: bad dims");
+        if (d < nd && (!(spacing[d] > 0.0f) || !std::isfinite(spacing[d])))
+            AC_FAIL(AC_ERR_ARG, "ac_server_submit: spacing must be positive");
+    }
+    Tile *t = new Tile();
+    std::memcpy(t->dims, dims, sizeof(t->dims));
+    std::memcpy(t->spacing, spacing, sizeof(t->spacing));
+    for (int d = nd; d < 3; ++d) t->spacing[d] = 1.0f;
+    t->data = data_host;
+    t->row_stride = row_stride;
+    t->plane_stride = plane_stride;
+    t->scale = intensity_scale;
+    t->stream_id = stream_id;
+    t->voxels = dims[0] * dims[1] * dims[2];
+    const int es = elem_bytes(S->p.dtype);
+    const int64_t pitch = (dims[0] * es + 15) / 16 * 16;
+    const int64_t C = lattice_contours(t->dims, t->spacing, nd, S->p.stride);
+    t->est_bytes = pitch * dims[1] * dims[2] + 100 * C + (1 << 20);
+    if (t->est_bytes > S->p.hbm_budget_bytes) {
+        delete t;
+        AC_FAIL(AC_ERR_BUDGET, "ac_server_submit: the tile alone exceeds the memory budget");
+    }
+    t->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete t;
+            AC_FAIL(AC_ERR_STATE, "ac_server_submit: server is stopping");
+        }
+        t->ticket = S->next_ticket++;
+        S->tiles[t->ticket] = t;
+        S->pending.push_back(t);
+    }
+    S->cv_work.notify_one();
+    *ticket = t->ticket;
+    return AC_OK;
+}
+
+extern "C" ac_status ac_server_wait(ac_server *S, int64_t ticket, double timeout_s, ac_cell *cells_out, int64_t cap,
+                                    ac_tile_result *result)
+{
+    if (!S || !result) AC_FAIL(AC_ERR_ARG, "ac_server_wait: NULL argument");
+    if (cap > 0 && !cells_out) AC_FAIL(AC_ERR_ARG, "ac_server_wait: cells_out is NULL");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tiles.find(ticket);
+    if (it == S->tiles.end()) AC_FAIL(AC_ERR_ARG, "ac_server_wait: unknown or collected ticket");
+    Tile *t = it->second;
+    auto ready = [&] { return t->done; };
+    if (timeout_s < 0) S->cv_done.wait(lk, ready);
+    else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready))
+        AC_FAIL(AC_ERR_TIMEOUT, "ac_server_wait: tile not finished yet");
+    std::memset(result, 0, sizeof(*result));
+    result->ticket = t->ticket;
+    result->status = t->status;
+    result->rounds = t->rounds;
+    result->n_cells = t->n_cells;
+    result->contours = t->contours;
+    result->voxels = t->voxels;
+    result->est_bytes = t->est_bytes;
+    const bool admitted = t->t_admit.time_since_epoch().count() != 0;
+    result->queue_ms = ms_between(t->t_submit, admitted ? t->t_admit : t->t_done);
+    result->run_ms = admitted ? ms_between(t->t_admit, t->t_done) : 0.0;
+    result->total_ms = ms_between(t->t_submit, t->t_done);
+    const int64_t n = std::min<int64_t>(cap, (int64_t)t->cells.size());
+    if (n > 0) std::memcpy(cells_out, t->cells.data(), sizeof(ac_cell) * (size_t)n);
+    const ac_status s = t->status;
+    const std::string err = t->error;
+    S->tiles.erase(it);
+    --S->finished;
+    delete t;
+    lk.unlock();
+    if (s != AC_OK) AC_FAIL(s, "tile " + std::to_string(ticket) + ": " + err);
+    return AC_OK;
+}
+
+extern "C" ac_status ac_server_get_stats(ac_server *S, ac_server_stats *out)
+{
+    if (!S || !out) AC_FAIL(AC_ERR_ARG, "ac_server_get_stats: NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->pending = (int64_t)S->pending.size();
+    out->resident = (int64_t)S->resident.size();
+    out->finished = S->finished;
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->rounds = S->rounds;
+    out->resident_bytes = S->resident_bytes;
+    out->peak_resident_bytes = S->peak_bytes;
+    out->budget_bytes = S->p.hbm_budget_bytes;
+    return AC_OK;
+}
+
+extern "C" void ac_server_destroy(ac_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->device);
+    cudaStreamSynchronize(S->st);
+    for (Tile *t : S->resident) release_device(t);
+    if (S->plan) ac_destroy_plan(S->plan);
+    for (auto &kv : S->tiles) delete kv.second;
+    cudaStreamDestroy(S->st);
+    delete S;
+}

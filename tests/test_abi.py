@@ -1,5 +1,5 @@
 """The C ABI library builds for sm_103a, loads without a GPU, exports every entry
-point include/ac.h declares, and rejects invalid arguments before touching the
+point include/*.h declares, and rejects invalid arguments before touching the
 device.  No compute call runs here."""
 import ctypes as ct
 import shutil
@@ -75,8 +75,14 @@ def test_struct_layouts_match_header(ac, tmp_path):
         "ac_seed_params": ["stride", "R0"],
         "ac_localize_params": ["E0"],
         "ac_batch_item": ["stream_id", "first_iter", "n_iter", "update_last"],
+        "ac_server_params": ["evolve", "dtype", "ndim", "stride", "R0", "E0", "iters_per_round", "max_resident",
+                             "hbm_budget_bytes"],
+        "ac_tile_result": ["ticket", "status", "rounds", "n_cells", "contours", "voxels", "est_bytes", "queue_ms",
+                           "run_ms", "total_ms"],
+        "ac_server_stats": ["pending", "resident", "finished", "completed", "failed", "rounds", "resident_bytes",
+                            "peak_resident_bytes", "budget_bytes"],
     }
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac.h"', "int main(void){"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac_serve.h"', "int main(void){"]
     for st, fields in checks.items():
         lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
         for f in fields:
@@ -95,3 +101,39 @@ def test_struct_layouts_match_header(ac, tmp_path):
         assert ct.sizeof(cls) == got[(st, "size")], st
         for f in fields:
             assert getattr(cls, f).offset == got[(st, f)], (st, f)
+
+
+def test_server_argument_validation_without_device(ac):
+    """ac_server_create checks every parameter before touching the device."""
+    l = ac.load()
+    good = ac.default_params(3, 4.0, 170.0, N=64, T=4)
+
+    def params(**kw):
+        sp = ac.ac_server_params()
+        sp.evolve = good.to_c()
+        sp.dtype, sp.ndim, sp.stride, sp.R0, sp.E0 = ac.AC_U8, 3, 4.0, 0.0, -10.0
+        sp.iters_per_round, sp.max_resident, sp.hbm_budget_bytes = 5, 0, 1 << 30
+        for k, v in kw.items():
+            if k == "N":
+                sp.evolve.N = v
+            else:
+                setattr(sp, k, v)
+        return sp
+
+    out = ct.c_void_p()
+    for bad in [dict(dtype=7), dict(ndim=4), dict(stride=0.0), dict(R0=-1.0), dict(E0=float("nan")),
+                dict(iters_per_round=0), dict(max_resident=-1), dict(hbm_budget_bytes=0), dict(N=0)]:
+        sp = params(**bad)
+        assert l.ac_server_create(ct.byref(sp), ct.byref(out)) == ac.AC_ERR_ARG, bad
+        assert not out.value
+    assert l.ac_server_create(None, ct.byref(out)) == ac.AC_ERR_ARG
+    t = ct.c_int64()
+    dims = (ct.c_int64 * 3)(4, 4, 4)
+    sp3 = (ct.c_float * 3)(1, 1, 1)
+    assert l.ac_server_submit(None, None, dims, 0, 0, sp3, 1.0, 0, ct.byref(t)) == ac.AC_ERR_ARG
+    r = ac.ac_tile_result()
+    assert l.ac_server_wait(None, 1, 0.0, None, 0, ct.byref(r)) == ac.AC_ERR_ARG
+    st = ac.ac_server_stats()
+    assert l.ac_server_get_stats(None, ct.byref(st)) == ac.AC_ERR_ARG
+    l.ac_server_destroy(None)
+    assert l.ac_plan_rebind(None, None, None, 0, None) == ac.AC_ERR_ARG

@@ -1,0 +1,139 @@
+"""Serving form: tiles of different sizes submitted over time to the request loop
+(include/ac_serve.h) give exactly the cells each gives when evolved alone through
+ac_create_volume / ac_seed / ac_evolve / ac_localize, whatever tiles share its
+rounds, under a tight memory budget, and with one tile that fails."""
+import dataclasses
+import math
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+STRIDE = 6.0
+CONTRAST = 1700.0
+T = 20
+
+
+@pytest.fixture(scope="module")
+def ac():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_06304_gb300 import ac as lib
+    lib.load()
+    return lib
+
+
+@pytest.fixture(scope="module")
+def tiles():
+    from paper_1804_06304_gb300 import synth
+    return [s for _, s in synth.tile_stream(21, count=6, max_scale=0.3)]
+
+
+def _params(ac):
+    return ac.default_params(3, STRIDE / math.sqrt(1.5), CONTRAST, N=128, T=T, seed=5)
+
+
+def _alone(ac, volume, spacing, params, stream_id):
+    V = ac.ac_create_volume(volume, spacing)
+    C = ac.ac_seed(V, stride=STRIDE)
+    ac.ac_evolve(C, dataclasses.replace(params, stream_id=stream_id))
+    return ac.ac_localize(C, ac.default_E0(3, CONTRAST))
+
+
+def _same_cells(a, b):
+    assert len(a) == len(b)
+    for f in a.dtype.names:
+        np.testing.assert_array_equal(a[f], b[f])
+
+
+def _est_bytes(volume, elem):
+    nz, ny, nx = volume.shape
+    pitch = (nx * elem + 15) // 16 * 16
+    C = max(1, int(nx // STRIDE)) * max(1, int(ny // STRIDE)) * max(1, int(nz // STRIDE))
+    return pitch * ny * nz + 100 * C + (1 << 20)
+
+
+def test_alone_equals_mix(ac, tiles):
+    p = _params(ac)
+    want = [_alone(ac, t.volume, t.spacing, p, 100 + i) for i, t in enumerate(tiles)]
+    srv = ac.Server(p, ac.AC_U16, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=120 << 30,
+                    iters_per_round=7)
+    tickets = []
+    for i, t in enumerate(tiles):
+        tickets.append(srv.submit(t.volume, t.spacing, stream_id=100 + i))
+        time.sleep(0.003 * i)          # staggered arrivals: tiles join at different rounds
+    for tk, w in zip(tickets, want):
+        cells, res = srv.wait(tk, timeout=300)
+        assert res["status"] == 0 and res["rounds"] == math.ceil(T / 7)
+        assert res["total_ms"] >= res["run_ms"] > 0 and res["n_cells"] == len(cells)
+        _same_cells(cells, w)
+    st = srv.stats()
+    assert st["completed"] == len(tiles) and st["resident"] == 0 and st["pending"] == 0 and st["finished"] == 0
+    assert st["rounds"] < len(tiles) * math.ceil(T / 7)   # rounds were shared
+    with pytest.raises(ac.ACError):
+        srv.wait(tickets[0], timeout=0)                   # collected already
+    srv.close()
+
+
+@pytest.mark.parametrize("mode", ["budget", "one_at_a_time"])
+def test_admission_limits(ac, tiles, mode):
+    p = _params(ac)
+    want = [_alone(ac, t.volume, t.spacing, p, 7 + i) for i, t in enumerate(tiles)]
+    est = [_est_bytes(t.volume, 2) for t in tiles]
+    budget = int(1.2 * max(est)) if mode == "budget" else 120 << 30
+    srv = ac.Server(p, ac.AC_U16, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=budget,
+                    iters_per_round=5, max_resident=1 if mode == "one_at_a_time" else 0)
+    tickets = [srv.submit(t.volume, t.spacing, stream_id=7 + i) for i, t in enumerate(tiles)]
+    for tk, w, e in zip(tickets, want, est):
+        cells, res = srv.wait(tk, timeout=300)
+        assert res["est_bytes"] == e
+        _same_cells(cells, w)
+    st = srv.stats()
+    assert st["peak_resident_bytes"] <= budget
+    if mode == "one_at_a_time":
+        assert st["peak_resident_bytes"] == max(est)
+        assert st["rounds"] == len(tiles) * math.ceil(T / 5)
+    else:
+        assert st["peak_resident_bytes"] < sum(est)       # the budget held tiles back
+        big = np.zeros((budget // (2 * 64 * 64) + 8, 64, 64), np.uint16)
+        with pytest.raises(ac.ACError) as e:
+            srv.submit(big, (1.0, 1.0, 1.0))
+        assert e.value.status == ac.AC_ERR_BUDGET
+    srv.close()
+
+
+def test_failing_tile_is_reported_alone(ac, tiles):
+    """A tile with non-finite voxels ends with AC_ERR_NUMERIC; the tiles that
+    shared its rounds are unaffected (each set keeps its own status word)."""
+    p = _params(ac)
+    vols = [t.volume[:40, :96, :96].astype(np.float32) for t in tiles[:3]]
+    bad = vols[1].copy()
+    bad[18:21, 40:43, 40:43] = np.nan
+    vols[1] = bad
+    want = {i: _alone(ac, vols[i], tiles[i].spacing, p, 50 + i) for i in (0, 2)}
+    srv = ac.Server(p, ac.AC_F32, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=1 << 30,
+                    iters_per_round=10)
+    tickets = [srv.submit(v, tiles[i].spacing, stream_id=50 + i) for i, v in enumerate(vols)]
+    for i, tk in enumerate(tickets):
+        if i == 1:
+            with pytest.raises(ac.ACError) as e:
+                srv.wait(tk, timeout=300)
+            assert e.value.status == ac.AC_ERR_NUMERIC
+        else:
+            cells, _ = srv.wait(tk, timeout=300)
+            _same_cells(cells, want[i])
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 2
+    srv.close()
+
+
+def test_destroy_with_tiles_in_flight(ac, tiles):
+    p = _params(ac)
+    srv = ac.Server(p, ac.AC_U16, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=120 << 30,
+                    iters_per_round=2)
+    for i, t in enumerate(tiles):
+        srv.submit(t.volume, t.spacing, stream_id=i)
+    srv.close()                                           # stops after the current round, frees everything
