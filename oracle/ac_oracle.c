@@ -217,7 +217,15 @@ typedef struct {
     double edge_tol;    /* band-edge proximity that flags a sample       */
     uint32_t key[2];    /* Philox key (seed low, seed high)              */
     uint32_t stream_id; /* fourth counter word                           */
-    uint32_t pad2_;
+    int32_t integration;/* 0: Monte-Carlo samples; 1: the voxel grid K of Eq. 5 */
+    /* stopping rules (0 disables each): a contour stops when its proposed step
+     * (largest coordinate change of c and R) is below freeze_tol for freeze_iters
+     * consecutive updates (that last step is not applied), or when its energy at
+     * iteration cull_iter is above cull_E (no update after it) */
+    double freeze_tol;
+    int32_t freeze_iters;
+    int32_t cull_iter;
+    double cull_E;
 } or_params;
 
 /* Result layout of or_eval_pq (doubles). */
@@ -246,6 +254,103 @@ static void sample_block(const or_params *P, int64_t blk, int64_t iter, int64_t 
     or_philox4x32_10(ctr, P->key, w);
 }
 
+/* Running sums over the points of K for one evaluation: the weighted sums of S I
+ * and of the partials of S with respect to p and q times I (Eqs. 5, 7-10), the
+ * magnitude sums that scale the parity tolerances, and raw moments of the
+ * per-point terms (for the Monte-Carlo variance). */
+typedef struct {
+    double sSI, sdpx, sdqx, sdpy, sdpz;
+    double mSI, mdSdR, mc[3], mg, mi;
+    double m1[5], m2[5];
+    int64_t flags, count;
+} or_sums;
+
+/* One point x of K with image value I and measure w, for the contour of centre c
+ * and radius R. */
+static void add_point(or_sums *A, const or_params *P, const double c[3], double R, const double edges[4],
+                      const double x[3], double I, double w)
+{
+    const int d = P->ndim;
+    double r2 = 0, dir[3] = {0, 0, 0}, Sw[3];
+    for (int a = 0; a < d; ++a) r2 += (x[a] - c[a]) * (x[a] - c[a]);
+    const double r = sqrt(r2);
+    if (r > 0)
+        for (int a = 0; a < d; ++a) dir[a] = (x[a] - c[a]) / r;
+    or_weight(d, r, R, P->dR, Sw);
+    const double S = Sw[0], dSdR = Sw[1], dSdr = Sw[2];
+    /* chain rule through r = |k - c|, c = (p + q)/2, R = (q_x - p_x)/2 */
+    const double dSdpx = dSdr * (-0.5 * dir[0]) + dSdR * (-0.5);
+    const double dSdqx = dSdr * (-0.5 * dir[0]) + dSdR * (+0.5);
+    const double dSdpy = dSdr * (-0.5 * dir[1]);
+    const double dSdpz = dSdr * (-0.5 * dir[2]);
+    A->sSI += w * S * I;
+    A->sdpx += w * dSdpx * I;
+    A->sdqx += w * dSdqx * I;
+    A->sdpy += w * dSdpy * I;
+    A->sdpz += w * dSdpz * I;
+    A->mSI += w * fabs(S * I);
+    A->mdSdR += w * fabs(dSdR * I);
+    for (int a = 0; a < d; ++a) A->mc[a] += w * fabs(dSdr * dir[a] * I);
+    A->mg += w * fabs(dSdr * I);
+    A->mi += w * fabs(I);
+    const double terms[5] = {S * I, (-(double)d / R * S + dSdR) * I, -dSdr * dir[0] * I, -dSdr * dir[1] * I,
+                             -dSdr * dir[2] * I};
+    for (int m = 0; m < 5; ++m) {
+        A->m1[m] += terms[m];
+        A->m2[m] += terms[m] * terms[m];
+    }
+    for (int e = 0; e < 4; ++e)
+        if (fabs(r - edges[e]) < P->edge_tol) {
+            ++A->flags;
+            break;
+        }
+    ++A->count;
+}
+
+/* Sums to E and its partials (Eqs. 6-11); mc_V > 0: Monte-Carlo with ball volume
+ * mc_V, which also gives the variance of each estimate. */
+static void finish_pq(const or_sums *A, const or_params *P, const double p[3], const double q[3], double mc_V,
+                      double *res)
+{
+    const int d = P->ndim;
+    const double R = 0.5 * (q[0] - p[0]);
+    const double L = q[0] - p[0];
+    const double gamma = 1.0 / pow(L, d);          /* Eq. 11 with exponent d */
+    memset(res, 0, sizeof(double) * OR_RES_LEN);
+    res[OR_E] = gamma * A->sSI;                                      /* Eq. 6 */
+    res[OR_DEDP + 0] = gamma * ((double)d / L * A->sSI + A->sdpx);  /* Eq. 7 */
+    res[OR_DEDQ + 0] = gamma * (-(double)d / L * A->sSI + A->sdqx); /* Eq. 8 */
+    res[OR_DEDP + 1] = res[OR_DEDQ + 1] = gamma * A->sdpy;           /* Eq. 9 */
+    res[OR_DEDP + 2] = res[OR_DEDQ + 2] = d == 3 ? gamma * A->sdpz : 0.0; /* Eq. 10 */
+    res[OR_DEDR] = res[OR_DEDQ + 0] - res[OR_DEDP + 0];
+    for (int a = 0; a < 3; ++a) res[OR_DEDC + a] = res[OR_DEDP + a] + res[OR_DEDQ + a];
+    res[OR_MAG_E] = gamma * A->mSI;
+    res[OR_MAG_R] = gamma * ((double)d / R * A->mSI + A->mdSdR);
+    for (int a = 0; a < 3; ++a) res[OR_MAG_C + a] = gamma * A->mc[a];
+    res[OR_FLAGS] = (double)A->flags;
+    res[OR_SUM_SI] = A->sSI;
+    res[OR_MAG_G] = gamma * A->mg;
+    res[OR_MAG_I] = gamma * A->mi;
+    if (mc_V > 0 && A->count > 0)
+        for (int m = 0; m < 5; ++m) {
+            /* each sample's term times gamma V is an unbiased one-sample estimate */
+            double mean = A->m1[m] / A->count, var = A->m2[m] / A->count - mean * mean;
+            double sc = gamma * mc_V;
+            res[OR_VAR_E + m] = (var > 0 ? var : 0) * sc * sc / A->count;
+        }
+}
+
+static void band_edges(const or_params *P, double R, double edges[4])
+{
+    const double rho = or_rho(P->ndim), dr = P->dR * rho;
+    edges[0] = rho * R - 0.5 * dr;
+    edges[1] = rho * R + 0.5 * dr;
+    edges[2] = R - 0.5 * P->dR;
+    edges[3] = R + 0.5 * P->dR;
+}
+
+/* Monte-Carlo form ("Monte-Carlo Integration" section): K is N uniform samples of
+ * the ball of radius R + dR/2, each of measure V/N. */
 void or_eval_pq(const or_image *img, const or_params *P, const double p[3], const double q[3],
                 int64_t iter, int64_t k, double *res)
 {
@@ -256,17 +361,13 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
     const double Ro = R + 0.5 * P->dR;             /* radius of K (Eq. 5) */
     const double V = d == 3 ? 4.0 / 3.0 * OR_PI * Ro * Ro * Ro : OR_PI * Ro * Ro;
     const double wmc = V / P->N;                   /* measure of one MC sample */
-    const double rho = or_rho(d), dr = P->dR * rho;
-    const double edges[4] = {rho * R - 0.5 * dr, rho * R + 0.5 * dr, R - 0.5 * P->dR, R + 0.5 * P->dR};
-
-    double sSI = 0, sdpx = 0, sdqx = 0, sdpy = 0, sdpz = 0;
-    double mSI = 0, mdSdR = 0, mc[3] = {0, 0, 0}, mg = 0, mi = 0;
-    /* raw moments of the per-sample terms, for the variance of the estimates */
-    double m1[5] = {0, 0, 0, 0, 0}, m2[5] = {0, 0, 0, 0, 0};
-    int64_t flags = 0;
+    double edges[4];
+    band_edges(P, R, edges);
+    or_sums A;
+    memset(&A, 0, sizeof(A));
     uint32_t w[4];
     for (int64_t j = 0; j < P->N; ++j) {
-        double u[3], x[3], dir[3] = {0, 0, 0}, Sw[3];
+        double u[3], x[3];
         if (d == 3) {
             sample_block(P, j, iter, k, w);
             or_unit_sample(3, w, 0, u);
@@ -276,60 +377,50 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
         }
         for (int a = 0; a < 3; ++a) x[a] = c[a] + Ro * u[a];
         if (d == 2) x[2] = c[2];
-        const double I = or_image_value(img, x);
-        double r2 = 0;
-        for (int a = 0; a < d; ++a) r2 += (x[a] - c[a]) * (x[a] - c[a]);
-        const double r = sqrt(r2);
-        if (r > 0)
-            for (int a = 0; a < d; ++a) dir[a] = (x[a] - c[a]) / r;
-        or_weight(d, r, R, P->dR, Sw);
-        const double S = Sw[0], dSdR = Sw[1], dSdr = Sw[2];
-        /* chain rule through r = |k - c|, c = (p + q)/2, R = (q_x - p_x)/2 */
-        const double dSdpx = dSdr * (-0.5 * dir[0]) + dSdR * (-0.5);
-        const double dSdqx = dSdr * (-0.5 * dir[0]) + dSdR * (+0.5);
-        const double dSdpy = dSdr * (-0.5 * dir[1]);
-        const double dSdpz = dSdr * (-0.5 * dir[2]);
-        sSI += wmc * S * I;
-        sdpx += wmc * dSdpx * I;
-        sdqx += wmc * dSdqx * I;
-        sdpy += wmc * dSdpy * I;
-        sdpz += wmc * dSdpz * I;
-        mSI += wmc * fabs(S * I);
-        mdSdR += wmc * fabs(dSdR * I);
-        for (int a = 0; a < d; ++a) mc[a] += wmc * fabs(dSdr * dir[a] * I);
-        mg += wmc * fabs(dSdr * I);
-        mi += wmc * fabs(I);
-        {
-            const double terms[5] = {S * I, (-(double)d / R * S + dSdR) * I, -dSdr * dir[0] * I,
-                                     -dSdr * dir[1] * I, -dSdr * dir[2] * I};
-            for (int m = 0; m < 5; ++m) { m1[m] += terms[m]; m2[m] += terms[m] * terms[m]; }
-        }
-        for (int e = 0; e < 4; ++e)
-            if (fabs(r - edges[e]) < P->edge_tol) { ++flags; break; }
+        add_point(&A, P, c, R, edges, x, or_image_value(img, x), wmc);
     }
-    const double L = q[0] - p[0];
-    const double gamma = 1.0 / pow(L, d);          /* Eq. 11 with exponent d */
-    memset(res, 0, sizeof(double) * OR_RES_LEN);
-    res[OR_E] = gamma * sSI;                                   /* Eq. 6 */
-    res[OR_DEDP + 0] = gamma * ((double)d / L * sSI + sdpx);  /* Eq. 7 */
-    res[OR_DEDQ + 0] = gamma * (-(double)d / L * sSI + sdqx); /* Eq. 8 */
-    res[OR_DEDP + 1] = res[OR_DEDQ + 1] = gamma * sdpy;        /* Eq. 9 */
-    res[OR_DEDP + 2] = res[OR_DEDQ + 2] = d == 3 ? gamma * sdpz : 0.0; /* Eq. 10 */
-    res[OR_DEDR] = res[OR_DEDQ + 0] - res[OR_DEDP + 0];
-    for (int a = 0; a < 3; ++a) res[OR_DEDC + a] = res[OR_DEDP + a] + res[OR_DEDQ + a];
-    res[OR_MAG_E] = gamma * mSI;
-    res[OR_MAG_R] = gamma * ((double)d / R * mSI + mdSdR);
-    for (int a = 0; a < 3; ++a) res[OR_MAG_C + a] = gamma * mc[a];
-    res[OR_FLAGS] = (double)flags;
-    res[OR_SUM_SI] = sSI;
-    res[OR_MAG_G] = gamma * mg;
-    res[OR_MAG_I] = gamma * mi;
-    for (int m = 0; m < 5; ++m) {
-        /* each sample's term times gamma V is an unbiased one-sample estimate */
-        double mean = m1[m] / P->N, var = m2[m] / P->N - mean * mean;
-        double s = gamma * V;
-        res[OR_VAR_E + m] = (var > 0 ? var : 0) * s * s / P->N;
+    finish_pq(&A, P, p, q, V, res);
+}
+
+/* Grid form, Eq. 5 taken literally (the paper's integration before Monte Carlo):
+ * K is every voxel centre k (index times spacing) with |k - c| <= R + dR/2, each of
+ * measure one voxel volume, the image extended beyond the volume by clamp-to-edge
+ * as for the samples. */
+void or_eval_grid_pq(const or_image *img, const or_params *P, const double p[3], const double q[3], double *res)
+{
+    const int d = P->ndim;
+    const double R = 0.5 * (q[0] - p[0]);
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = 0.5 * (p[a] + q[a]);
+    const double Ro = R + 0.5 * P->dR;
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    double vox = 1.0;
+    for (int a = 0; a < d; ++a) {
+        lo[a] = (int64_t)ceil((c[a] - Ro) / img->spacing[a]);
+        hi[a] = (int64_t)floor((c[a] + Ro) / img->spacing[a]);
+        vox *= img->spacing[a];
     }
+    double edges[4];
+    band_edges(P, R, edges);
+    or_sums A;
+    memset(&A, 0, sizeof(A));
+    for (int64_t kk = lo[2]; kk <= hi[2]; ++kk)
+        for (int64_t j = lo[1]; j <= hi[1]; ++j)
+            for (int64_t i = lo[0]; i <= hi[0]; ++i) {
+                double x[3] = {i * img->spacing[0], j * img->spacing[1], d == 3 ? kk * img->spacing[2] : c[2]};
+                double r2 = 0;
+                for (int a = 0; a < d; ++a) r2 += (x[a] - c[a]) * (x[a] - c[a]);
+                if (r2 > Ro * Ro) continue;
+                add_point(&A, P, c, R, edges, x, or_image_value(img, x), vox);
+            }
+    finish_pq(&A, P, p, q, 0.0, res);
+}
+
+static void eval_any(const or_image *img, const or_params *P, const double p[3], const double q[3], int64_t iter,
+                     int64_t k, double *res)
+{
+    if (P->integration == 1) or_eval_grid_pq(img, P, p, q, res);
+    else or_eval_pq(img, P, p, q, iter, k, res);
 }
 
 /* Same evaluation from the centre/radius form of the state. */
@@ -337,7 +428,7 @@ void or_eval_cr(const or_image *img, const or_params *P, const double c[3], doub
                 int64_t iter, int64_t k, double *res)
 {
     double p[3] = {c[0] - R, c[1], c[2]}, q[3] = {c[0] + R, c[1], c[2]};
-    or_eval_pq(img, P, p, q, iter, k, res);
+    eval_any(img, P, p, q, iter, k, res);
 }
 
 /* Eq. 5 taken literally: the sum over the voxel grid K inside R + dR/2, times the
@@ -421,8 +512,13 @@ enum { OR_TRACE_LEN = 9 };
  * the energy of the final state; trace (T x C x 9, optional) records every
  * evaluation.  Contours are independent (the "Parallelizing the process" section),
  * so they are spread over `nthreads` OpenMP threads. */
+/* T iterations per contour: evaluate, then update (Eqs. 12-15), with the
+ * stopping rules of or_params.  `stops` (optional): 0 ran all T iterations, 1
+ * stopped by the step rule, 2 stopped by the energy rule; `n_eval` (optional):
+ * evaluations made.  A stopped contour keeps the state and energy of its last
+ * evaluation; trace rows after it are left untouched. */
 void or_evolve(const or_image *img, const or_params *P, int64_t C, const int64_t *ids,
-               double *cR, double *E_out, double *trace, int nthreads)
+               double *cR, double *E_out, double *trace, int32_t *stops, int32_t *n_eval, int nthreads)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -432,8 +528,10 @@ void or_evolve(const or_image *img, const or_params *P, int64_t C, const int64_t
         double p[3] = {cR[4 * i] - cR[4 * i + 3], cR[4 * i + 1], cR[4 * i + 2]};
         double q[3] = {cR[4 * i] + cR[4 * i + 3], cR[4 * i + 1], cR[4 * i + 2]};
         double res[OR_RES_LEN];
+        int32_t stop = 0, evals = 0, small = 0;
         for (int64_t n = 1; n <= P->T; ++n) {
-            or_eval_pq(img, P, p, q, n, ids[i], res);
+            eval_any(img, P, p, q, n, ids[i], res);
+            evals = (int32_t)n;
             if (trace) {
                 double *t = trace + ((n - 1) * C + i) * OR_TRACE_LEN;
                 t[0] = 0.5 * (p[0] + q[0]); t[1] = p[1]; t[2] = p[2];
@@ -441,13 +539,35 @@ void or_evolve(const or_image *img, const or_params *P, int64_t C, const int64_t
                 t[4] = res[OR_E]; t[5] = res[OR_DEDR];
                 t[6] = res[OR_DEDC]; t[7] = res[OR_DEDC + 1]; t[8] = res[OR_DEDC + 2];
             }
-            if (n < P->T) or_update_pq(img, P, n, res, p, q);
+            if (P->cull_iter > 0 && n == P->cull_iter && res[OR_E] > P->cull_E) {
+                stop = 2;
+                break;
+            }
+            if (n == P->T) break;
+            double pn[3] = {p[0], p[1], p[2]}, qn[3] = {q[0], q[1], q[2]};
+            or_update_pq(img, P, n, res, pn, qn);
+            if (P->freeze_iters > 0) {
+                double step = fabs(0.5 * (qn[0] - pn[0]) - 0.5 * (q[0] - p[0]));   /* |dR| */
+                for (int a = 0; a < P->ndim; ++a) {
+                    double ca = 0.5 * (p[a] + q[a]), cn = 0.5 * (pn[a] + qn[a]);
+                    if (fabs(cn - ca) > step) step = fabs(cn - ca);
+                }
+                small = step < P->freeze_tol ? small + 1 : 0;
+                if (small >= P->freeze_iters) {
+                    stop = 1;
+                    break;
+                }
+            }
+            memcpy(p, pn, sizeof(p));
+            memcpy(q, qn, sizeof(q));
         }
         cR[4 * i] = 0.5 * (p[0] + q[0]);
         cR[4 * i + 1] = p[1];
         cR[4 * i + 2] = p[2];
         cR[4 * i + 3] = 0.5 * (q[0] - p[0]);
         E_out[i] = res[OR_E];
+        if (stops) stops[i] = stop;
+        if (n_eval) n_eval[i] = evals;
     }
 }
 

@@ -58,7 +58,9 @@ class Params(ct.Structure):
         ("ndim", ct.c_int32), ("N", ct.c_int32), ("T", ct.c_int32), ("pad_", ct.c_int32),
         ("eps0", ct.c_double), ("dR", ct.c_double), ("Rmin", ct.c_double), ("Rmax", ct.c_double),
         ("max_step", ct.c_double), ("edge_tol", ct.c_double),
-        ("key", ct.c_uint32 * 2), ("stream_id", ct.c_uint32), ("pad2_", ct.c_uint32),
+        ("key", ct.c_uint32 * 2), ("stream_id", ct.c_uint32), ("integration", ct.c_int32),
+        ("freeze_tol", ct.c_double), ("freeze_iters", ct.c_int32), ("cull_iter", ct.c_int32),
+        ("cull_E", ct.c_double),
     ]
 
 
@@ -87,7 +89,9 @@ def lib():
                 "or_eval_cr": (None, [IP, PP, D, ct.c_double, ct.c_int64, ct.c_int64, D]),
                 "or_energy_grid": (ct.c_double, [IP, ct.c_int, D, ct.c_double, ct.c_double]),
                 "or_update_pq": (None, [IP, PP, ct.c_int64, D, D, D]),
-                "or_evolve": (None, [IP, PP, ct.c_int64, I64, D, D, D, ct.c_int]),
+                "or_evolve": (None, [IP, PP, ct.c_int64, I64, D, D, D, ct.POINTER(ct.c_int32),
+                                     ct.POINTER(ct.c_int32), ct.c_int]),
+                "or_eval_grid_pq": (None, [IP, PP, D, D, D]),
                 "or_max_threads": (ct.c_int, []),
                 "or_seed_lattice": (ct.c_int64, [ct.c_int, I64, D, ct.c_double, D]),
                 "or_localize": (ct.c_int64, [ct.c_int, ct.c_int64, D, D, ct.c_double, I64]),
@@ -144,8 +148,14 @@ class BlobImage:
 
 
 def make_params(ndim, N, T=1, eps0=0.0, dR=1.0, Rmin=0.5, Rmax=1e9, max_step=0.5, seed=0, stream_id=0,
-                edge_tol=1e-5) -> Params:
+                edge_tol=1e-5, integration=0, freeze_tol=0.0, freeze_iters=0, cull_iter=0, cull_E=0.0) -> Params:
+    """integration 0: Monte-Carlo samples, 1: the voxel grid of Eq. 5.  Stopping
+    rules (0 disables): freeze after ``freeze_iters`` consecutive proposed steps
+    below ``freeze_tol``; stop at iteration ``cull_iter`` when E > ``cull_E``."""
     p = Params()
+    p.integration, p.freeze_tol, p.freeze_iters, p.cull_iter, p.cull_E = (int(integration), float(freeze_tol),
+                                                                           int(freeze_iters), int(cull_iter),
+                                                                           float(cull_E))
     p.ndim, p.N, p.T = ndim, N, T
     p.eps0, p.dR, p.Rmin, p.Rmax, p.max_step, p.edge_tol = eps0, dR, Rmin, Rmax, max_step, edge_tol
     p.key[0] = seed & 0xFFFFFFFF
@@ -204,6 +214,15 @@ def eval_pq(img, params, p, q, it, k) -> np.ndarray:
     return res
 
 
+def eval_grid_pq(img, params, p, q) -> np.ndarray:
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    res = np.empty(RES_LEN)
+    lib().or_eval_grid_pq(ct.byref(img.s), ct.byref(params), _P(p, ct.c_double), _P(q, ct.c_double),
+                          _P(res, ct.c_double))
+    return res
+
+
 def eval_cr(img, params, c, R, it, k) -> np.ndarray:
     c = np.ascontiguousarray(list(c) + [0.0] * (3 - len(c)), dtype=np.float64)
     res = np.empty(RES_LEN)
@@ -238,16 +257,21 @@ def update_pq(img, params, it, res, p, q):
     return p, q
 
 
-def evolve(img, params, cR: np.ndarray, ids=None, trace: bool = False, nthreads: int = 0):
-    """Returns (final cR (C x 4), E (C,), trace (T x C x 9) or None)."""
+def evolve(img, params, cR: np.ndarray, ids=None, trace: bool = False, nthreads: int = 0, stops: bool = False):
+    """Returns (final cR (C x 4), E (C,), trace (T x C x 9) or None), and with
+    ``stops`` also (stop reason (C,): 0 none, 1 step rule, 2 energy rule;
+    evaluations made (C,)).  Trace rows after a stop are NaN."""
     cR = np.array(cR, dtype=np.float64, order="C").reshape(-1, 4)   # a C-ordered copy (updated in place)
     C = len(cR)
     ids = np.arange(C, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
     E = np.empty(C)
-    tr = np.empty((params.T, C, TRACE_LEN)) if trace else None
+    tr = np.full((params.T, C, TRACE_LEN), np.nan) if trace else None
+    st = np.zeros(C, dtype=np.int32)
+    ne = np.zeros(C, dtype=np.int32)
     lib().or_evolve(ct.byref(img.s), ct.byref(params), C, _P(ids, ct.c_int64), _P(cR, ct.c_double),
-                    _P(E, ct.c_double), _P(tr, ct.c_double) if trace else None, nthreads)
-    return cR, E, tr
+                    _P(E, ct.c_double), _P(tr, ct.c_double) if trace else None, _P(st, ct.c_int32),
+                    _P(ne, ct.c_int32), nthreads)
+    return (cR, E, tr, st, ne) if stops else (cR, E, tr)
 
 
 def max_threads() -> int:

@@ -15,6 +15,10 @@ fix, never against itself.
 * Invariants: constant image, linear ramp, integer translation.
 * Brute force on a tiny random volume: dense quadrature of S * I over the ball.
 * Convergence on a noise-free blob, lattice spacing (Fig. 1b), localization rules.
+* Grid form of Eq. 5: convergence to the exact energy as the grid refines, partials
+  equal to central differences of the grid energy, integer translation.
+* Stopping rules (step and energy), pinned to their definitions: limits that make
+  them equivalent to a shorter fixed-T run or to no rule at all.
 """
 import math
 import os
@@ -523,3 +527,117 @@ def test_localize_rules(oracle):
     cR = np.array([[0, 0, 0, 4.0], [RHO2 * 4.0 * 0.999, 0, 0, 4.0]])
     assert list(oracle.localize(2, cR, np.array([-1.0, -2.0]), 0.0)) == [1]
     assert len(oracle.localize(3, np.zeros((0, 4)), np.zeros(0), 0.0)) == 0
+
+
+# ----------------------------------------------------------------------------- grid form of Eq. 5
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("R", [4.0, 5.6, 6.5])
+def test_grid_energy_converges_to_exact(oracle, ndim, R):
+    """The voxel-grid sum of Eq. 5 on an ideal blob sampled at spacing h tends to
+    the exact finite-band energy (quadrature) as h -> 0."""
+    exact = _exact_concentric(oracle, ndim, R, 5.0, 170.0, 1.0)
+    errs = []
+    for h in (0.5, 0.0625):
+        img = oracle.BlobImage(ndim, (0.0, 0.0, 0.0)[:ndim], 5.0, 170.0, offset=30.0)
+        img.s.spacing[:] = (h, h, h)
+        res = oracle.eval_cr(img, oracle.make_params(ndim, 1, integration=1), [0.0] * ndim, R, 1, 0)
+        errs.append(abs(res[oracle.E] - exact) / res[oracle.MAG_E])
+    assert errs[1] < 3e-3, errs
+    assert errs[1] < errs[0] or errs[0] < 1e-3, errs
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_grid_partials_are_derivatives_of_grid_energy(oracle, ndim):
+    """dE/dR and dE/dc of the grid form (Eqs. 7-10 over the voxel grid) equal
+    central differences of the grid energy itself, on a random anisotropic volume."""
+    rng = np.random.default_rng(31 + ndim)
+    shape = (14, 15, 16)[:ndim]
+    vol = rng.integers(0, 255, size=shape, dtype=np.uint8)
+    sp = (1.0, 1.25, 2.0) if ndim == 3 else (1.0, 1.25, 1.0)
+    img = oracle.VolumeImage(vol, sp)
+    P = oracle.make_params(ndim, 1, integration=1)
+    h = 1e-6
+    for trial in range(6):
+        c = [rng.uniform(4.0, 9.0) for _ in range(ndim)]
+        R = rng.uniform(2.5, 4.5)
+        res = oracle.eval_cr(img, P, c, R, 1, 0)
+        if res[oracle.FLAGS] > 0:
+            continue
+        E = lambda cc, RR: oracle.eval_cr(img, P, cc, RR, 1, 0)[oracle.E]
+        dR = (E(c, R + h) - E(c, R - h)) / (2 * h)
+        assert abs(res[oracle.DEDR] - dR) < 1e-6 * res[oracle.MAG_R], (trial, res[oracle.DEDR], dR)
+        for a in range(ndim):
+            cp = list(c); cm = list(c)
+            cp[a] += h; cm[a] -= h
+            dc = (E(cp, R) - E(cm, R)) / (2 * h)
+            assert abs(res[oracle.DEDC + a] - dc) < 1e-6 * res[oracle.MAG_G], (trial, a, res[oracle.DEDC + a], dc)
+        # the energy is the literal Eq. 5 grid sum
+        assert abs(res[oracle.E] - oracle.energy_grid(img, ndim, c + [0.0] * (3 - ndim), R, 1.0)) < 1e-12 * \
+            res[oracle.MAG_E] + 1e-12
+
+
+def test_grid_integer_translation_invariance(oracle):
+    rng = np.random.default_rng(9)
+    vol = rng.integers(0, 255, size=(20, 24, 28), dtype=np.uint8)
+    big = np.zeros((26, 34, 42), dtype=np.uint8)
+    big[3:23, 5:29, 7:35] = vol
+    P = oracle.make_params(3, 1, integration=1)
+    a = oracle.eval_cr(oracle.VolumeImage(vol), P, [13.3, 11.7, 9.2], 4.1, 5, 123)
+    b = oracle.eval_cr(oracle.VolumeImage(big), P, [20.3, 16.7, 12.2], 4.1, 5, 123)
+    np.testing.assert_allclose(a[:11], b[:11], rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- stopping rules
+def _stop_case(oracle):
+    from paper_1804_06304_gb300 import synth
+    vol = synth.sphere_volume((32, 32, 32), (15.6, 16.3, 15.9), 5.0, 200.0, 30.0)
+    img = oracle.VolumeImage(vol)
+    R0 = 4.0 / math.sqrt(1.5)
+    seeds = np.array([[15.6 + dx, 16.3 - dx, 15.9 + 0.5 * dx, R0] for dx in (0.0, 0.8, 1.6, 2.4)])
+    kw = dict(eps0=8 * R0**2 / 170.0, max_step=0.5, Rmin=R0 / 2, Rmax=3 * R0, seed=4)
+    return img, seeds, kw
+
+
+def test_freeze_rule_limits(oracle):
+    """freeze_tol huge: every contour stops after freeze_iters evaluations with the
+    state and energy of a fixed run of T = freeze_iters (the last proposed step is
+    not applied); freeze_tol = 0: identical to no rule."""
+    img, seeds, kw = _stop_case(oracle)
+    base = oracle.evolve(img, oracle.make_params(3, 64, 30, **kw), seeds, stops=True)
+    short = oracle.evolve(img, oracle.make_params(3, 64, 3, **kw), seeds)
+    big = oracle.evolve(img, oracle.make_params(3, 64, 30, freeze_tol=1e9, freeze_iters=3, **kw), seeds, stops=True)
+    np.testing.assert_array_equal(big[0], short[0])
+    np.testing.assert_array_equal(big[1], short[1])
+    assert (big[3] == 1).all() and (big[4] == 3).all()
+    zero = oracle.evolve(img, oracle.make_params(3, 64, 30, freeze_tol=0.0, freeze_iters=1, **kw), seeds, stops=True)
+    np.testing.assert_array_equal(zero[0], base[0])
+    assert (zero[3] == 0).all() and (zero[4] == 30).all() and (base[4] == 30).all()
+
+
+def test_energy_rule_limits(oracle):
+    """cull_E = -inf: every contour stops at cull_iter with the state of a fixed run
+    of T = cull_iter; cull_E = +inf: identical to no rule."""
+    img, seeds, kw = _stop_case(oracle)
+    base = oracle.evolve(img, oracle.make_params(3, 64, 30, **kw), seeds)
+    short = oracle.evolve(img, oracle.make_params(3, 64, 5, **kw), seeds)
+    allc = oracle.evolve(img, oracle.make_params(3, 64, 30, cull_iter=5, cull_E=-np.inf, **kw), seeds, stops=True)
+    np.testing.assert_array_equal(allc[0], short[0])
+    np.testing.assert_array_equal(allc[1], short[1])
+    assert (allc[3] == 2).all() and (allc[4] == 5).all()
+    none = oracle.evolve(img, oracle.make_params(3, 64, 30, cull_iter=5, cull_E=np.inf, **kw), seeds, stops=True)
+    np.testing.assert_array_equal(none[0], base[0])
+    assert (none[3] == 0).all()
+
+
+def test_freeze_rule_stops_converged_contours_early(oracle):
+    """On a noise-free blob the contours converge, their steps (Monte-Carlo noise
+    times the decaying eps_n) shrink below the tolerance and they stop before T,
+    still on the blob centre."""
+    img, seeds, kw = _stop_case(oracle)
+    cR, E, tr, st, ne = oracle.evolve(img, oracle.make_params(3, 256, 200, freeze_tol=0.1, freeze_iters=4, **kw),
+                                      seeds, trace=True, stops=True)
+    assert (st == 1).all() and (ne < 200).all(), ne
+    assert np.all(np.linalg.norm(cR[:, :3] - np.array([15.6, 16.3, 15.9]), axis=1) < 0.25)
+    for i in range(len(seeds)):   # trace rows stop at the last evaluation, which is the final state
+        assert np.isnan(tr[ne[i]:, i]).all() and not np.isnan(tr[:ne[i], i]).any()
+        np.testing.assert_array_equal(tr[ne[i] - 1, i, :4], cR[i])
