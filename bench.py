@@ -230,7 +230,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large-2d", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default="native", choices=["native", "f16"])
-    ap.add_argument("--path", default="brick", choices=["brick", "plain"])
+    ap.add_argument("--path", default="brick", choices=["brick", "plain", "grid"],
+                    help="grid: the voxel-grid form of Eq. 5 instead of Monte-Carlo samples")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--compensated", type=int, default=1)
     ap.add_argument("--brick", type=str, default="0,0,0")
@@ -279,7 +280,8 @@ def main(argv=None):
     assert C.count == C_expected, (C.count, C_expected)
     R0 = wl["stride"] / math.sqrt(1.5)
     params = ac.default_params(ndim, R0, s.contrast, N=wl["N"], T=wl["T"], seed=1000 + rank,
-                               path=ac.AC_PATH_BRICK if args.path == "brick" else ac.AC_PATH_PLAIN,
+                               path={"brick": ac.AC_PATH_BRICK, "plain": ac.AC_PATH_PLAIN,
+                                     "grid": ac.AC_PATH_GRID}[args.path],
                                lanes_per_contour=args.lanes, compensated=args.compensated,
                                brick=tuple(int(x) for x in args.brick.split(",")), warps_per_block=args.warps,
                                halo_factor=args.halo)
@@ -356,11 +358,28 @@ def main(argv=None):
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.path != "grid":
         v, thr, desc = oracle_sample(s, vol, wl, spacing, args.cpu_seconds)
         cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc}
+    citers = C.count * wl["T"]
 
-    if rank == 0:
+    if rank == 0 and args.path == "grid":
+        # the grid form has no samples: throughput in contour-iterations
+        _, gval = aggregate_ranks(step_ms, citers, world, reducer)
+        print(json.dumps({
+            "metric": "contour-iterations/s (voxel-grid form of Eq. 5; whole path: ingest, seed, evolve, localize)",
+            "value": gval, "unit": "contour-iterations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 arithmetic on " + str(vol.dtype) + " voxels", "data": "synthetic",
+            "config": {"workload": args.workload + (f"@{args.size}" if args.size else ""), "desc": wl["desc"],
+                       "contours": C.count, "iterations": wl["T"], "path": "grid",
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "contour_iterations_per_s": gval, "evolve_kernel_ms": k_ms,
+            "evolve_contour_iterations_per_s": world * citers / (k_ms * 1e-3), "cells": n_cells,
+            "gpu_launches": int(launches), "roofline": None, "cpu_baseline": None,
+            "e2e": None if e2e is None else dict(e2e, value=e2e["value"] / wl["N"], unit="contour-iterations/s"),
+            "clocks": clk}))
+    elif rank == 0:
         line = {
             "metric": "MC contour samples/s (whole path: ingest, seed, evolve, localize)",
             "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -372,6 +391,7 @@ def main(argv=None):
                        "parallelism": f"replicas x{world}"},
             "voxels_per_s": world * int(np.prod(vol.shape)) / (t_ms * 1e-3),
             "evolve_samples_per_s": world * samples / (k_ms * 1e-3),
+            "contour_iterations_per_s": world * citers / (t_ms * 1e-3),
             "cells": n_cells,
             "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
             "gpu_launches": int(launches),

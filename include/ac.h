@@ -48,7 +48,12 @@ typedef enum { AC_U8 = 0, AC_U16 = 1, AC_F16 = 2, AC_F32 = 3 } ac_dtype;
 typedef enum {
     AC_PATH_BRICK = 0,   /* bricks + halo staged in shared memory by 3D TMA, one
                             persistent pass over all T iterations (default)        */
-    AC_PATH_PLAIN = 1    /* one launch per iteration, gathers from global memory    */
+    AC_PATH_PLAIN = 1,   /* one launch per iteration, gathers from global memory    */
+    AC_PATH_GRID = 2     /* Eq. 5 on the voxel grid (the paper's integration before
+                            Monte Carlo): the sums run over every voxel centre within
+                            R + dR/2, each of measure one voxel volume, instead of N
+                            samples (N is ignored); one pass over all iterations,
+                            gathers from global memory                              */
 } ac_path;
 
 typedef struct ac_volume ac_volume;
@@ -105,7 +110,8 @@ int64_t ac_contour_count(const ac_contours *ctr);
 void ac_destroy_contours(ac_contours *ctr);
 
 /* ac_reseed -- write the lattice of a lattice-seeded handle again (same stride and
- * R0, energies zero) and clear its status word; no allocation.  Asynchronous.
+ * R0, energies zero) and clear its status word and the stopping-rule state of
+ * every contour; no allocation.  Asynchronous.
  * Errors: AC_ERR_ARG, AC_ERR_STATE (handle seeded explicitly), AC_ERR_CUDA. */
 ac_status ac_reseed(ac_contours *ctr, void *cuda_stream);
 
@@ -127,7 +133,15 @@ ac_status ac_reseed(ac_contours *ctr, void *cuda_stream);
  *            to the box of voxel centres.
  * Iterations run from n = first_iter to first_iter + T - 1; the update after the
  * last one is applied only when update_last is set.  Afterwards each contour holds
- * its centre and radius and the energy of its last evaluation.  Arithmetic is
+ * its centre and radius and the energy of its last evaluation.
+ * Stopping rules (convergence freeze and energy culling; 0 disables each): a
+ * contour stops when the step an update proposes (the largest absolute change of
+ * a centre coordinate or of R, after the clamps) is below freeze_tol for
+ * freeze_iters consecutive updates -- that last step is not applied -- or when its
+ * energy at iteration cull_iter is above cull_E (no update follows).  A stopped
+ * contour keeps the state and energy of its last evaluation and is skipped by
+ * later calls until ac_reseed or ac_set_state; the count of consecutive small
+ * steps carries over between calls, so resumed runs equal uninterrupted ones.  Arithmetic is
  * FP32 with compensated sums; volumes are read as stored (uint8/uint16/FP16/FP32).  `trace` (optional) records the state
  * and results of every evaluation for contours k in [k_begin, k_end) and
  * iterations n in [t_begin, t_end).  Asynchronous on the stream.
@@ -161,6 +175,10 @@ typedef struct {
     float halo_factor;         /* brick halo = halo_factor x the largest initial radius
                                   + dR/2 + 2 voxels (0 = auto); balls that outgrow it
                                   read the global volume for that iteration           */
+    float freeze_tol;          /* step below which an update counts as small (>= 0)   */
+    int32_t freeze_iters;      /* consecutive small steps that stop a contour (0: off) */
+    int32_t cull_iter;         /* iteration whose energy is tested (0: off)           */
+    float cull_E;              /* a contour with E > cull_E at cull_iter stops        */
 } ac_evolve_params;
 
 typedef struct {
@@ -300,8 +318,9 @@ ac_status ac_localize(ac_contours *ctr, const ac_localize_params *params, ac_cel
  * 5 x C float32, structure of arrays: cx[C], cy[C], cz[C], R[C], E[C].  With the
  * counter-based generator, setting a saved state and evolving from iteration n
  * reproduces an uninterrupted run (see first_iter / update_last).  ac_set_state
- * clamps centres into the box of voxel centres and needs radii in (0, 1e6];
- * ac_get_state synchronizes the stream and
+ * clamps centres into the box of voxel centres, needs radii in (0, 1e6] and
+ * clears the stopping-rule state (see ac_evolve); ac_get_state synchronizes the
+ * stream and
  * reports the status word.  Errors: AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_TIMEOUT,
  * AC_ERR_NUMERIC.
  */
@@ -321,6 +340,11 @@ ac_status ac_philox4x32_10(const uint32_t *ctr_dev, uint64_t key, uint32_t *out_
  * events recorded by the library on the launching stream, inside the graph for a
  * graph launch; binning and sorting excluded).  Synchronizes on the end event.  Errors: AC_ERR_ARG, AC_ERR_STATE (nothing evolved yet), AC_ERR_CUDA. */
 ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms);
+
+/* Contours of this handle stopped by the step rule (counts[0]) and by the energy
+ * rule (counts[1]) of ac_evolve_params so far.  Synchronizes the stream.
+ * Errors: AC_ERR_ARG, AC_ERR_CUDA. */
+ac_status ac_evolve_stops(ac_contours *ctr, int64_t counts[2], void *cuda_stream);
 
 /* Contour-iterations of the last ac_evolve / ac_evolve_batch on this handle by
  * gather path: counts[0] fast (ball inside the staged region and the volume),

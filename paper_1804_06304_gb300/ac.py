@@ -19,7 +19,7 @@ from . import build as _build
 
 AC_OK, AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STATE, AC_ERR_TIMEOUT, AC_ERR_BUDGET, AC_ERR_NUMERIC = range(8)
 AC_U8, AC_U16, AC_F16, AC_F32 = range(4)
-AC_PATH_BRICK, AC_PATH_PLAIN = 0, 1
+AC_PATH_BRICK, AC_PATH_PLAIN, AC_PATH_GRID = 0, 1, 2
 STATUS_NAMES = {0: "AC_OK", 1: "AC_ERR_ARG", 2: "AC_ERR_OOM", 3: "AC_ERR_CUDA", 4: "AC_ERR_STATE",
                 5: "AC_ERR_TIMEOUT", 6: "AC_ERR_BUDGET", 7: "AC_ERR_NUMERIC"}
 
@@ -40,7 +40,8 @@ class ac_evolve_params(ct.Structure):
                 ("stream_id", ct.c_uint32), ("path", ct.c_int32), ("lanes_per_contour", ct.c_int32),
                 ("compensated", ct.c_int32), ("brick", ct.c_int32 * 3), ("warps_per_block", ct.c_int32),
                 ("first_iter", ct.c_int32), ("update_last", ct.c_int32), ("sampling", ct.c_int32),
-                ("halo_factor", ct.c_float)]
+                ("halo_factor", ct.c_float), ("freeze_tol", ct.c_float), ("freeze_iters", ct.c_int32),
+                ("cull_iter", ct.c_int32), ("cull_E", ct.c_float)]
 
 
 class ac_trace(ct.Structure):
@@ -104,6 +105,7 @@ _SIGS = {
     "ac_evolve_kernel_ms": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_float)]),
     "ac_kernel_launches": (ct.c_int64, []),
     "ac_evolve_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p]),
+    "ac_evolve_stops": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p]),
     "ac_evolve_static": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
                                     ct.POINTER(ct.c_float), ct.c_float, ct.c_void_p, ct.c_int64, ct.c_float,
                                     ct.c_float, ct.POINTER(ac_evolve_params), ct.c_void_p]),
@@ -300,6 +302,10 @@ class EvolveParams:
     update_last: int = 0
     sampling: int = 0
     halo_factor: float = 0.0
+    freeze_tol: float = 0.0
+    freeze_iters: int = 0
+    cull_iter: int = 0
+    cull_E: float = 0.0
 
     def to_c(self) -> ac_evolve_params:
         p = ac_evolve_params()
@@ -316,8 +322,9 @@ def default_params(ndim: int, R0: float, contrast: float, N: int, T: int, seed: 
     expected foreground-background contrast in scaled intensity), dR = 1,
     Rmin = max(dR/2, R0/2), Rmax = 3 R0, max_step = 0.5."""
     dR = kw.pop("dR", 1.0)
-    return EvolveParams(N=N, T=T, eps0=8.0 * R0 * R0 / contrast, dR=dR, Rmin=max(0.5 * dR, 0.5 * R0), Rmax=3.0 * R0,
-                        seed=seed, **kw)
+    base = dict(eps0=8.0 * R0 * R0 / contrast, dR=dR, Rmin=max(0.5 * dR, 0.5 * R0), Rmax=3.0 * R0)
+    base.update(kw)   # explicit values win
+    return EvolveParams(N=N, T=T, seed=seed, **base)
 
 
 def default_E0(ndim: int, contrast: float) -> float:
@@ -459,6 +466,13 @@ def ac_evolve_stats(ctr: Contours, stream=None) -> tuple:
     c = (ct.c_int64 * 3)()
     _check(load().ac_evolve_stats(ctr.handle, c, ct.c_void_p(_stream(stream))))
     return tuple(int(v) for v in c)
+
+
+def ac_evolve_stops(ctr: Contours, stream=None) -> tuple:
+    """(contours stopped by the step rule, by the energy rule) so far."""
+    out = (ct.c_int64 * 2)()
+    _check(load().ac_evolve_stops(ctr.handle, out, ct.c_void_p(_stream(stream))))
+    return int(out[0]), int(out[1])
 
 
 def ac_kernel_launches() -> int:

@@ -177,10 +177,15 @@ static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out)
     cudaError_t e = cudaMalloc(&c->state, sizeof(float) * 5 * (size_t)(C > 0 ? C : 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->hold, sizeof(int32_t) * (size_t)(C > 0 ? C : 1));
+    if (e == cudaSuccess) e = cudaMemset(c->hold, 0, sizeof(int32_t) * (size_t)(C > 0 ? C : 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->path_counts, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMemset(c->path_counts, 0, sizeof(unsigned long long) * 4);
     if (e != cudaSuccess) {
         if (c->state) cudaFree(c->state);
+        if (c->status) cudaFree(c->status);
+        if (c->hold) cudaFree(c->hold);
+        if (c->path_counts) cudaFree(c->path_counts);
         delete c;
         AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
                 std::string("ac_seed: allocation: ") + cudaGetErrorString(e));
@@ -272,6 +277,7 @@ extern "C" ac_status ac_reseed(ac_contours *c, void *cuda_stream)
     const int64_t C = c->C;
     const int64_t blocks = std::min<int64_t>((C + threads - 1) / threads, 1 << 16);
     AC_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int32_t) * 4, st));
+    AC_CUDA(cudaMemsetAsync(c->hold, 0, sizeof(int32_t) * (size_t)(C > 0 ? C : 1), st));
     seed_lattice_kernel<<<(unsigned)blocks, threads, 0, st>>>(c->state, C, (int)c->L[0], (int)c->L[1], c->first[0],
                                                               c->first[1], c->first[2], c->stride, c->R0,
                                                               c->vol->ndim);
@@ -290,6 +296,7 @@ extern "C" void ac_destroy_contours(ac_contours *ctr)
     if (ctr->ev1) cudaEventDestroy(ctr->ev1);
     cudaFree(ctr->state);
     cudaFree(ctr->status);
+    cudaFree(ctr->hold);
     cudaFree(ctr->path_counts);
     delete ctr;
 }
@@ -303,6 +310,8 @@ static ac_status check_status(ac_contours *ctr, cudaStream_t st)
     if (s[0] & STATUS_TMA_TIMEOUT) AC_FAIL(AC_ERR_TIMEOUT, "device status: a brick load did not complete in time");
     if (s[0] & STATUS_LOCALIZE_LIMIT) AC_FAIL(AC_ERR_TIMEOUT, "device status: localization round bound reached");
     if (s[0] & STATUS_NONFINITE) AC_FAIL(AC_ERR_NUMERIC, "device status: non-finite contour state");
+    if (s[0] & STATUS_GRID_RANGE)
+        AC_FAIL(AC_ERR_ARG, "device status: a contour radius exceeded the grid path's bound (contour stopped)");
     return AC_OK;
 }
 
@@ -330,6 +339,7 @@ extern "C" ac_status ac_set_state(ac_contours *ctr, const float *in_host, void *
     }
     AC_CUDA(cudaMemcpyAsync(ctr->state, st.data(), sizeof(float) * 5 * C, cudaMemcpyHostToDevice,
                             (cudaStream_t)cuda_stream));
+    AC_CUDA(cudaMemsetAsync(ctr->hold, 0, sizeof(int32_t) * (size_t)(C > 0 ? C : 1), (cudaStream_t)cuda_stream));
     AC_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
     return AC_OK;
 }
@@ -377,7 +387,7 @@ struct Plan {
     int quad_off;   // 2D: byte offset of the float4 quads (0: none)
     int smem;       // dynamic shared memory bytes
     int G, warps;
-    bool brick, comp, acc;
+    bool brick, grid, comp, acc;
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -405,7 +415,15 @@ ac_status check_params(const ac_evolve_params *p)
         AC_FAIL(AC_ERR_ARG, "ac_evolve: need 0 < Rmin <= Rmax");
     if (!(p->max_step > 0.0f) || !std::isfinite(p->max_step)) AC_FAIL(AC_ERR_ARG, "ac_evolve: max_step must be positive");
     if (!(p->eps0 >= 0.0f) || !std::isfinite(p->eps0)) AC_FAIL(AC_ERR_ARG, "ac_evolve: eps0 must be >= 0");
-    if (p->path != AC_PATH_BRICK && p->path != AC_PATH_PLAIN) AC_FAIL(AC_ERR_ARG, "ac_evolve: unknown path");
+    if (p->path != AC_PATH_BRICK && p->path != AC_PATH_PLAIN && p->path != AC_PATH_GRID)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: unknown path");
+    if (p->path == AC_PATH_GRID && p->lanes_per_contour != 0 && p->lanes_per_contour != 8 &&
+        p->lanes_per_contour != 16)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: the grid path takes 8 or 16 lanes per contour");
+    if (!(p->freeze_tol >= 0.0f) || !std::isfinite(p->freeze_tol)) AC_FAIL(AC_ERR_ARG, "ac_evolve: freeze_tol must be >= 0");
+    if (p->freeze_iters < 0 || p->freeze_iters > 0xFFFF) AC_FAIL(AC_ERR_ARG, "ac_evolve: freeze_iters in [0, 65535]");
+    if (p->cull_iter < 0) AC_FAIL(AC_ERR_ARG, "ac_evolve: cull_iter must be >= 0");
+    if (std::isnan(p->cull_E)) AC_FAIL(AC_ERR_ARG, "ac_evolve: cull_E is NaN");
     if (p->sampling < 0 || p->sampling > 2) AC_FAIL(AC_ERR_ARG, "ac_evolve: sampling must be 0, 1 or 2");
     if (!(p->halo_factor >= 0.0f) || p->halo_factor > 64.0f) AC_FAIL(AC_ERR_ARG, "ac_evolve: halo_factor in [0, 64]");
     if (p->first_iter < 0 || (int64_t)(p->first_iter ? p->first_iter : 1) + p->T > (1 << 30))
@@ -416,7 +434,8 @@ ac_status check_params(const ac_evolve_params *p)
     if (p->lanes_per_contour == 4 && (p->compensated == 0 || p->sampling == 1 || (p->sampling == 0 && p->N < 64)))
         AC_FAIL(AC_ERR_ARG, "ac_evolve: 4 lanes per contour are built for compensated sums and fast sampling");
     if (p->warps_per_block < 0 || p->warps_per_block > 16) AC_FAIL(AC_ERR_ARG, "ac_evolve: warps_per_block in [0, 16]");
-    if (p->path == AC_PATH_PLAIN && p->warps_per_block > 8) AC_FAIL(AC_ERR_ARG, "ac_evolve: plain path takes at most 8 warps per block");
+    if (p->path != AC_PATH_BRICK && p->warps_per_block > 8)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: the plain and grid paths take at most 8 warps per block");
     for (int d = 0; d < 3; ++d)
         if (p->brick[d] < 0 || p->brick[d] > 224) AC_FAIL(AC_ERR_ARG, "ac_evolve: brick sizes must be in [0, 224]");
     return AC_OK;
@@ -431,7 +450,15 @@ ac_status check_params(const ac_evolve_params *p)
 ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, const ac_evolve_params *p, Plan &pl)
 {
     pl.brick = p->path == AC_PATH_BRICK;
+    pl.grid = p->path == AC_PATH_GRID;
     pl.comp = p->compensated != 0;
+    if (pl.grid) {   // no samples: no sampling mode; lanes walk the chords of the ball
+        pl.acc = false;
+        pl.G = p->lanes_per_contour ? p->lanes_per_contour : 8;
+        pl.warps = p->warps_per_block ? p->warps_per_block : 8;
+        pl.quad_off = 0;
+        return AC_OK;
+    }
     pl.acc = p->sampling == 1 || (p->sampling == 0 && p->N < 64);
     if (pl.acc && !pl.comp) AC_FAIL(AC_ERR_ARG, "ac_evolve: accurate sampling is built with compensated sums only");
     // lanes per contour: about 32 samples per lane (4 lanes only with compensated
@@ -564,6 +591,7 @@ VolDesc make_desc(const ac_contours *c, uint32_t stream)
     d.scale = v->scale;
     d.state = c->state;
     d.status = c->status;
+    d.hold = c->hold;
     d.C = c->C;
     d.stream = stream;
     return d;
@@ -683,8 +711,20 @@ ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int
         a.kr1 = (float)(-2.0 / dr);
         a.kr2 = (float)(1.0 / dR);
         a.vol_coef = (float)((d == 3 ? 4.0 / 3.0 * M_PI : M_PI) / p->N);
+        a.freeze_tol = p->freeze_tol;
+        a.freeze_iters = p->freeze_iters;
+        a.cull_iter = p->cull_iter;
+        a.cull_E = p->cull_E;
     }
     a.path_counts = sets[0]->path_counts;
+    if (pl.grid)   // bounded work per evaluation
+        for (int i = 0; i < n_sets; ++i)
+            for (int d = 0; d < sets[i]->vol->ndim; ++d) {
+                const double lim = (double)GRID_MAX_RADIUS_VOXELS * sets[i]->vol->sp[d];
+                if ((double)p->Rmax + 0.5 * p->dR > lim || sets[i]->r_hint + 0.5 * p->dR > lim)
+                    AC_FAIL(AC_ERR_ARG, "ac_evolve: the grid path takes balls of at most 256 voxels radius "
+                                        "(Rmax + dR/2 and the seeded radii)");
+            }
 
     pr.desc.assign(n_sets, VolDesc());
     int64_t bricks = 0, cbase = 0;
@@ -786,7 +826,15 @@ ac_status enqueue_prepared(Prepared &pr, Scratch &sc, cudaStream_t st, int64_t *
     ac_contours *owner = pr.owner;
     int64_t nl = 0;
     AC_CUDA(cudaMemsetAsync(owner->path_counts, 0, sizeof(unsigned long long) * 3, st));
-    if (!pr.pl.brick) {
+    if (pr.pl.grid) {
+        const int64_t per_cta = (int64_t)pr.pl.warps * 32 / pr.pl.G;
+        const int64_t grid = std::min<int64_t>((pr.total + per_cta - 1) / per_cta, (int64_t)1 << 30);
+        AC_CUDA(cudaEventRecordWithFlags(owner->ev0, st, ev_flags));
+        cudaError_t e = launch_grid(pr.dtype, a, pr.pl.G, pr.pl.comp, pr.pl.warps, grid, st);
+        if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: grid launch: ") + cudaGetErrorString(e));
+        ++nl;
+        AC_CUDA(cudaEventRecordWithFlags(owner->ev1, st, ev_flags));
+    } else if (!pr.pl.brick) {
         const int64_t per_cta = (int64_t)pr.pl.warps * 32 / pr.pl.G;
         const int64_t grid = std::min<int64_t>((pr.total + per_cta - 1) / per_cta, (int64_t)1 << 30);
         AC_CUDA(cudaEventRecordWithFlags(owner->ev0, st, ev_flags));
@@ -882,6 +930,8 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
     if (!volume_dev || !state_dev || !dims || !spacing) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: NULL argument");
     ac_status s = check_params(p);
     if (s != AC_OK) return s;
+    if (p->path == AC_PATH_GRID || p->freeze_iters > 0 || p->cull_iter > 0)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve_static: takes the brick and plain paths without stopping rules");
     const int es = elem_size(dtype);
     if (es == 0) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: unknown dtype");
     if (ndim != 2 && ndim != 3) AC_FAIL(AC_ERR_ARG, "ac_evolve_static: ndim must be 2 or 3");
@@ -1128,7 +1178,8 @@ extern "C" ac_status ac_plan_set_items(ac_plan *pl, const ac_batch_item *items, 
     AC_CUDA(cudaMemcpyAsync(pl->sc.desc.p, pl->pr.desc.data(), sizeof(VolDesc) * pl->pr.n_sets,
                             cudaMemcpyHostToDevice, (cudaStream_t)cuda_stream));
     // a captured plain-path graph holds one launch per iteration of its span
-    if (!pl->pr.pl.brick && (pl->pr.a.first_iter != pl->span0 || pl->pr.a.last_iter != pl->span1)) drop_graph(pl);
+    if (!pl->pr.pl.brick && !pl->pr.pl.grid && (pl->pr.a.first_iter != pl->span0 || pl->pr.a.last_iter != pl->span1))
+        drop_graph(pl);
     return AC_OK;
 }
 
@@ -1284,6 +1335,8 @@ extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_ev
             tp.T = std::min(params->T, 3);
             tp.first_iter = 1;
             tp.update_last = 0;
+            tp.freeze_iters = 0;   // trials time the full work of every contour
+            tp.cull_iter = 0;
             double per = 1.0;
             for (int d = 0; d < 3; ++d) {
                 tp.brick[d] = d < v0->ndim ? std::max(1, (int)std::lround(cl[d] * stride_hint / v0->sp[d])) : 0;
@@ -1345,6 +1398,46 @@ extern "C" ac_status ac_evolve_stats(ac_contours *ctr, int64_t counts[3], void *
     AC_CUDA(cudaMemcpyAsync(c, ctr->path_counts, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream));
     AC_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
     for (int i = 0; i < 3; ++i) counts[i] = (int64_t)c[i];
+    return AC_OK;
+}
+
+namespace {
+__global__ void count_stops_kernel(const int32_t *hold, int64_t C, unsigned long long *out)
+{
+    unsigned int f = 0, c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t h = hold[i];
+        f += (h & HOLD_FROZEN) ? 1u : 0u;
+        c += (h & HOLD_CULLED) ? 1u : 0u;
+    }
+    f = __reduce_add_sync(0xffffffffu, f);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) {
+        if (f) atomicAdd(&out[0], (unsigned long long)f);
+        if (c) atomicAdd(&out[1], (unsigned long long)c);
+    }
+}
+}  // namespace
+
+extern "C" ac_status ac_evolve_stops(ac_contours *ctr, int64_t counts[2], void *cuda_stream)
+{
+    g_err.clear();
+    if (!ctr || !counts) AC_FAIL(AC_ERR_ARG, "ac_evolve_stops: NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    AC_CUDA(ctr->scratch.counters.ensure(2 * sizeof(unsigned long long)));
+    unsigned long long *d = ctr->scratch.counters.as<unsigned long long>();
+    AC_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
+    const int64_t blocks = std::min<int64_t>((ctr->C + 255) / 256, 1024);
+    if (ctr->C > 0) {
+        count_stops_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(ctr->hold, ctr->C, d);
+        count_launch();
+        AC_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[2] = {0, 0};
+    AC_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    AC_CUDA(cudaStreamSynchronize(st));
+    counts[0] = (int64_t)h[0];
+    counts[1] = (int64_t)h[1];
     return AC_OK;
 }
 

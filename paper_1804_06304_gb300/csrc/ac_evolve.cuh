@@ -401,6 +401,46 @@ __device__ __forceinline__ void update(const Step &s, int n, const EvolveArgs &a
     for (int i = 0; i < DIM; ++i) c[i] = fminf(fmaxf(c[i] + d[i], 0.0f), box_hi[i]);
 }
 
+// Stopping rules, then the update after evaluation n.  The energy rule stops a
+// contour whose energy at iteration cull_iter is above cull_E; the step rule
+// counts consecutive updates whose step (largest absolute change of a centre
+// coordinate or R, after the clamps) is below freeze_tol and stops the contour,
+// without that step, when the count reaches freeze_iters.  Every lane of a group
+// holds the same sums, so the decision is uniform over the group.  Returns true
+// when the contour stops.
+template <int DIM>
+__device__ __forceinline__ bool step_or_stop(const Step &s, int n, const EvolveArgs &a, const VolDesc &V, float *c,
+                                             float &R, int32_t &h)
+{
+    if (a.cull_iter > 0 && n == a.cull_iter && s.E > a.cull_E) {
+        h |= HOLD_CULLED;
+        return true;
+    }
+    if (!(n < V.last_iter || V.update_last)) return false;
+    if (a.freeze_iters <= 0) {
+        update<DIM>(s, n, a, V.box_hi, c, R);
+        return false;
+    }
+    float cn[3] = {c[0], c[1], c[2]}, Rn = R;
+    update<DIM>(s, n, a, V.box_hi, cn, Rn);
+    float step = fabsf(Rn - R);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) step = fmaxf(step, fabsf(cn[d] - c[d]));
+    const int32_t cnt = step < a.freeze_tol ? min((h & HOLD_COUNT) + 1, (int32_t)HOLD_COUNT) : 0;
+    h = (h & ~HOLD_COUNT) | cnt;
+    if (cnt >= a.freeze_iters) {
+        h |= HOLD_FROZEN;
+        return true;
+    }
+    c[0] = cn[0];
+    c[1] = cn[1];
+    c[2] = cn[2];
+    R = Rn;
+    return false;
+}
+
+__device__ __forceinline__ bool rules_on(const EvolveArgs &a) { return a.freeze_iters > 0 || a.cull_iter > 0; }
+
 // A non-finite evaluation (non-finite voxels) freezes the contour and is reported
 // through the status word rather than pushed through the clamps.
 __device__ __forceinline__ bool finite_step(const Step &s)
@@ -464,7 +504,7 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *keys, int64_t
 // the volume and the region), the clamped shared-memory path (ball crosses the
 // volume border) or, when the ball has left the region, global-memory gathers.
 template <int DIM, typename T, int G, bool COMP, bool ACC>
-__global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant__ EvolveArgs a)
+__global__ void __maxnreg__(DIM == 2 ? 80 : 128) evolve_brick_kernel(const __grid_constant__ EvolveArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
@@ -522,6 +562,8 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
 
     for (int64_t i = cb + grp; i < ce; i += ngrp) {
         const int64_t k = (int64_t)a.sorted_gidx[i] - V.contour_base;
+        int32_t h = V.hold ? V.hold[k] : 0;
+        if (h & HOLD_STOPPED) continue;   // stopped by a rule in an earlier call
         float c[3] = {V.state[k], V.state[C + k], DIM == 3 ? V.state[2 * C + k] : 0.0f};
         float R = V.state[3 * C + k];
         Step s;
@@ -573,7 +615,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
                 if (lig == 0) atomicOr(V.status, STATUS_NONFINITE);
                 break;
             }
-            if (n < V.last_iter || V.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
+            if (step_or_stop<DIM>(s, n, a, V, c, R, h)) break;
         }
         if (lig == 0) {
             V.state[k] = c[0];
@@ -583,6 +625,7 @@ __global__ void __launch_bounds__(512) evolve_brick_kernel(const __grid_constant
             V.state[4 * C + k] = s.E;
             if (!(isfinite(s.E) && isfinite(R) && isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2])))
                 atomicOr(V.status, STATUS_NONFINITE);
+            if (V.hold && rules_on(a)) V.hold[k] = h;
         }
     }
     // one atomic per warp and path: sum the groups' counts over the warp
@@ -611,6 +654,8 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
         if (n < V.first_iter || n > V.last_iter) continue;   // outside this set's iterations
         const int64_t k = gi - V.contour_base;
         const int64_t C = V.C;
+        int32_t h = V.hold ? V.hold[k] : 0;
+        if (h & HOLD_STOPPED) continue;
         float c[3] = {V.state[k], V.state[C + k], DIM == 3 ? V.state[2 * C + k] : 0.0f};
         float R = V.state[3 * C + k];
         IterC<DIM> ic;
@@ -622,7 +667,8 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
             ++glob;
             write_trace(a, v, k, n, c, R, s);
             if (!finite_step(s)) atomicOr(V.status, STATUS_NONFINITE);
-            else if (n < V.last_iter || V.update_last) update<DIM>(s, n, a, V.box_hi, c, R);
+            else step_or_stop<DIM>(s, n, a, V, c, R, h);
+            if (V.hold && rules_on(a)) V.hold[k] = h;
             V.state[k] = c[0];
             V.state[C + k] = c[1];
             if (DIM == 3) V.state[2 * C + k] = c[2];

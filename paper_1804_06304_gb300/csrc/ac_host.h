@@ -58,13 +58,14 @@ struct Scratch {
 }  // namespace ac
 
 struct ac_contours {
-    ac_volume *vol;
-    int64_t C;
-    float *state;         // 5 x C
-    int32_t *status;      // device status word
-    unsigned long long *path_counts;   // device [3]: contour-iterations per gather path
-    double stride_hint;   // lattice stride (or mean spacing of explicit seeds)
-    double r_hint;        // largest initial radius
+    ac_volume *vol = nullptr;
+    int64_t C = 0;
+    float *state = nullptr;              // 5 x C
+    int32_t *status = nullptr;           // device status word
+    int32_t *hold = nullptr;             // device [C]: stopping-rule state per contour
+    unsigned long long *path_counts = nullptr;   // device [3]: contour-iterations per gather path
+    double stride_hint = 0;   // lattice stride (or mean spacing of explicit seeds)
+    double r_hint = 0;        // largest initial radius
     ac::Scratch scratch;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last evolution kernel(s)
     bool lattice = false;                       // lattice-seeded: parameters below
@@ -89,6 +90,9 @@ cudaError_t launch_evolve_f16(const EvolveArgs &a, bool brick, int G, bool comp,
                               cudaStream_t st);
 cudaError_t launch_evolve_f32(const EvolveArgs &a, bool brick, int G, bool comp, bool acc, int warps, int64_t grid,
                               cudaStream_t st);
+
+// the voxel-grid form of Eq. 5 (ac_grid.cu)
+cudaError_t launch_grid(ac_dtype t, const EvolveArgs &a, int G, bool comp, int warps, int64_t grid, cudaStream_t st);
 
 // the argument checks of ac_evolve (ac_api.cu)
 ac_status check_evolve_params(const ac_evolve_params *p);

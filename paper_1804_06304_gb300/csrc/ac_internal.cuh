@@ -15,7 +15,22 @@ namespace ac {
 enum : int32_t {
     STATUS_TMA_TIMEOUT = 1,   // a brick's TMA load did not complete within the bound
     STATUS_NONFINITE = 2,     // a contour's state or energy became non-finite
-    STATUS_LOCALIZE_LIMIT = 4 // localization rounds hit their bound
+    STATUS_LOCALIZE_LIMIT = 4,// localization rounds hit their bound
+    STATUS_GRID_RANGE = 8     // grid path: a ball wider than the grid bound (contour stopped)
+};
+
+// Grid path: largest ball radius, in voxels along any axis, that an evaluation
+// may cover (bounds the work of one evaluation).
+constexpr float GRID_MAX_RADIUS_VOXELS = 256.0f;
+
+// ----------------------------------------------------------------- stopping rules
+// Per-contour hold word: the count of consecutive small steps (low 16 bits) and
+// the rule that stopped the contour, if any.
+enum : int32_t {
+    HOLD_COUNT = 0xFFFF,
+    HOLD_FROZEN = 1 << 30,    // stopped by the step rule
+    HOLD_CULLED = 1 << 29,    // stopped by the energy rule
+    HOLD_STOPPED = HOLD_FROZEN | HOLD_CULLED
 };
 
 // ----------------------------------------------------------------- structures
@@ -32,6 +47,7 @@ struct VolDesc {
     int32_t nb[3];       // bricks per axis (brick path)
     float *state;        // 5 x C float32, SoA: cx, cy, cz, R, E
     int32_t *status;     // this set's sticky status word
+    int32_t *hold;       // per-contour hold words (nullptr: no stopping state)
     int64_t C;           // contours in this set
     int64_t brick_base;  // first global brick index of this set
     int64_t contour_base;// first global contour index of this set
@@ -70,6 +86,10 @@ struct EvolveArgs {
     float kR1, kR2;      // dS/dR on the inner / outer band
     float kr1, kr2;      // -dS/dr on the inner / outer band
     float vol_coef;      // (4/3 pi or pi) / N: ball measure per sample, over Ro^d
+    float freeze_tol;    // stopping rules (0: off)
+    int32_t freeze_iters;
+    int32_t cull_iter;
+    float cull_E;
     float *trace;        // optional (volume 0 only)
     int64_t tk0, tk1;
     int32_t tt0, tt1;

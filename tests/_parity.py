@@ -25,7 +25,9 @@ REL = 1e-5
 def oracle_params(oracle, ndim, p, edge_tol=1e-5):
     f = lambda x: float(np.float32(x))
     return oracle.make_params(ndim, p.N, p.T, eps0=f(p.eps0), dR=f(p.dR), Rmin=f(p.Rmin), Rmax=f(p.Rmax),
-                              max_step=f(p.max_step), seed=p.seed, stream_id=p.stream_id, edge_tol=edge_tol)
+                              max_step=f(p.max_step), seed=p.seed, stream_id=p.stream_id, edge_tol=edge_tol,
+                              integration=1 if p.path == 2 else 0, freeze_tol=f(p.freeze_tol),
+                              freeze_iters=p.freeze_iters, cull_iter=p.cull_iter, cull_E=f(p.cull_E))
 
 
 def oracle_image(oracle, volume, spacing, scale=1.0):
@@ -61,7 +63,11 @@ def teacher_forced(oracle, img, op, trace, k0, t0, nthreads=0):
     rows = trace.reshape(-1, 9).astype(np.float64)
     iters = np.repeat(np.arange(t0, t0 + T), K)
     ks = np.tile(np.arange(k0, k0 + K), T)
-    res = oracle.eval_many(img, op, rows[:, :4], iters, ks, nthreads=nthreads)
+    # rows the kernel never wrote (after a contour stopped) stay NaN and are skipped
+    valid = ~np.isnan(rows[:, :4]).any(axis=1)
+    res = np.full((len(rows), oracle.RES_LEN), np.nan)
+    res[valid] = oracle.eval_many(img, op, rows[valid, :4], iters[valid], ks[valid], nthreads=nthreads)
+    res[~valid, oracle.FLAGS] = 1.0   # excluded like flagged rows
     ok = np.ones(len(rows), bool)
     d = 3 if op.ndim == 3 else 2
     mag_e = res[:, oracle.MAG_I]
@@ -72,12 +78,12 @@ def teacher_forced(oracle, img, op, trace, k0, t0, nthreads=0):
     for gc, oc, mag in pairs:
         tol = REL * np.maximum(np.abs(res[:, oc]), mag) + 1e-30
         err = np.abs(rows[:, gc] - res[:, oc])
-        ok &= err <= tol
-        worst = max(worst, float(np.max(np.where(res[:, oracle.FLAGS] > 0, 0, err / tol))))
-    flagged = res[:, oracle.FLAGS] > 0
-    good = ok[~flagged]
+        ok &= (err <= tol) | ~valid
+        worst = max(worst, float(np.max(np.where((res[:, oracle.FLAGS] > 0) | ~valid, 0, err / tol))))
+    flagged = (res[:, oracle.FLAGS] > 0) & valid
+    good = ok[~flagged & valid]
     frac = float(good.mean()) if len(good) else 1.0
-    bad = np.nonzero(~ok & ~flagged)[0][:10]
+    bad = np.nonzero(~ok & ~flagged & valid)[0][:10]
     details = [(int(iters[i]), int(ks[i]), rows[i, 4:].tolist(), res[i, [0, 7, 8, 9, 10]].tolist()) for i in bad]
     return frac, int(flagged.sum()), worst, details, res
 

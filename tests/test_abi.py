@@ -69,7 +69,8 @@ def test_struct_layouts_match_header(ac, tmp_path):
     checks = {
         "ac_evolve_params": ["N", "T", "eps0", "dR", "Rmin", "Rmax", "max_step", "seed", "stream_id", "path",
                              "lanes_per_contour", "compensated", "brick", "warps_per_block", "first_iter",
-                             "update_last", "sampling", "halo_factor"],
+                             "update_last", "sampling", "halo_factor", "freeze_tol", "freeze_iters", "cull_iter",
+                             "cull_E"],
         "ac_trace": ["device_buf", "k_begin", "k_end", "t_begin", "t_end"],
         "ac_cell": ["c", "r", "E", "id"],
         "ac_seed_params": ["stride", "R0"],
@@ -137,3 +138,19 @@ def test_server_argument_validation_without_device(ac):
     assert l.ac_server_get_stats(None, ct.byref(st)) == ac.AC_ERR_ARG
     l.ac_server_destroy(None)
     assert l.ac_plan_rebind(None, None, None, 0, None) == ac.AC_ERR_ARG
+
+
+def test_static_path_rejects_grid_and_rules_without_device(ac):
+    l = ac.load()
+    dims = (ct.c_int64 * 3)(8, 8, 8)
+    sp = (ct.c_float * 3)(1, 1, 1)
+    fake = ct.c_void_p(0x1000)   # never dereferenced: the arguments are refused first
+    for kw in (dict(path=ac.AC_PATH_GRID), dict(freeze_iters=2, freeze_tol=0.1), dict(cull_iter=3)):
+        p = ac.default_params(3, 3.0, 100.0, N=64, T=4, **kw).to_c()
+        assert l.ac_evolve_static(fake, 0, 3, dims, 0, 0, sp, 1.0, fake, 8, 3.0, 4.0, ct.byref(p), None) == \
+            ac.AC_ERR_ARG, kw
+    for kw in (dict(freeze_tol=-1.0), dict(freeze_iters=-1), dict(cull_iter=-2), dict(cull_E=float("nan")),
+               dict(path=3), dict(path=ac.AC_PATH_GRID, lanes_per_contour=32)):
+        p = ac.default_params(3, 3.0, 100.0, N=64, T=4, **kw).to_c()
+        assert l.ac_evolve_static(fake, 0, 3, dims, 0, 0, sp, 1.0, fake, 8, 3.0, 4.0, ct.byref(p), None) == \
+            ac.AC_ERR_ARG, kw
