@@ -22,6 +22,7 @@ contours never interact across images); the step time is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -46,6 +47,10 @@ import numpy as np  # noqa: E402
 # sample; eight 8/16-bit taps with exact integer-to-float conversion).  The
 # per-iteration reduction and update are excluded.  Tabulated in the design notes.
 ALG_SLOTS_PER_SAMPLE = {2: 76.0, 3: 147.0}
+# dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
+# ncu capture of the current kernel (to be removed when the kernel changes): the
+# 2048^2 instance read 7.05 MB, scaled by 4 with the image area and contour count.
+DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.2e6}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0
@@ -238,6 +243,8 @@ def main(argv=None):
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--halo", type=float, default=0.0, help="halo factor (0 = library default)")
     ap.add_argument("--size", type=int, default=0, help="image side (smaller instances for profiling captures)")
+    ap.add_argument("--freeze", type=str, default="", help="TOL,ITERS: convergence freeze rule (off by default)")
+    ap.add_argument("--cull", type=str, default="", help="ITER,FRAC: stop contours with E > FRAC x E0 at ITER")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -286,6 +293,14 @@ def main(argv=None):
                                brick=tuple(int(x) for x in args.brick.split(",")), warps_per_block=args.warps,
                                halo_factor=args.halo)
     E0 = ac.default_E0(ndim, s.contrast)
+    rules = {}
+    if args.freeze:
+        tol, its = args.freeze.split(",")
+        rules.update(freeze_tol=float(tol), freeze_iters=int(its))
+    if args.cull:
+        it, frac = args.cull.split(",")
+        rules.update(cull_iter=int(it), cull_E=float(frac) * E0)
+    params = dataclasses.replace(params, **rules)
 
     def step(src):
         ac.ac_load_volume(V, src)
@@ -328,7 +343,9 @@ def main(argv=None):
     torch.cuda.synchronize()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    samples = C.count * wl["N"] * wl["T"]
+    # with stopping rules only the evaluated contour-iterations count (the speed-up
+    # of stopping shows in voxels/s)
+    samples = (int(sum(paths)) if rules else C.count * wl["T"]) * wl["N"]
     reducer = torch_max_reducer(dev) if dist_on else None
     t_ms, value = aggregate_ranks(step_ms, samples, world, reducer)
     k_ms, _ = aggregate_ranks(kernel_ms, samples, world, reducer)
@@ -352,8 +369,11 @@ def main(argv=None):
 
     achieved = ALG_SLOTS_PER_SAMPLE[ndim] * samples / (k_ms * 1e-3) / 1e12
     peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = DRAM_BYTES_PER_LAUNCH.get((args.workload, args.path, args.size, args.dtype))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
+            "traffic": traffic,
+            "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: ncu capture of the "
+                            "2048^2 instance scaled x4 with the area", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
             "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
 
@@ -387,11 +407,14 @@ def main(argv=None):
             "dtype": "f32 arithmetic on " + str(vol.dtype) + " voxels", "data": "synthetic",
             "config": {"workload": args.workload + (f"@{args.size}" if args.size else ""), "desc": wl["desc"],
                        "contours": C.count, "samples": wl["N"],
-                       "iterations": wl["T"], "path": args.path, "l2": "flushed between timed steps (256 MB write)",
+                       "iterations": wl["T"], "path": args.path, "stopping_rules": rules or None,
+                       "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "voxels_per_s": world * int(np.prod(vol.shape)) / (t_ms * 1e-3),
             "evolve_samples_per_s": world * samples / (k_ms * 1e-3),
             "contour_iterations_per_s": world * citers / (t_ms * 1e-3),
+            "evaluated_contour_iterations": int(sum(paths)),
+            "stopped": dict(zip(("freeze", "cull"), ac.ac_evolve_stops(C))) if rules else None,
             "cells": n_cells,
             "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
             "gpu_launches": int(launches),

@@ -482,8 +482,9 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     const int64_t budget = vol->ndim == 3 ? 110 * 1024 : 200 * 1024;
     int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
     for (int d = 0; d < vol->ndim; ++d) {
-        // lattice cells per brick: 2x2x2 in 3D, 12x8 in 2D (measured best for 128 samples)
-        const double cells = vol->ndim == 3 ? 2.0 : (d == 0 ? 12.0 : 8.0);
+        // lattice cells per brick: 2x2x2 in 3D, 10x8 in 2D (measured best for 128
+        // samples: 80 contours of 4 lanes fill 10 warps, two CTAs per SM at 96 registers)
+        const double cells = vol->ndim == 3 ? 2.0 : (d == 0 ? 10.0 : 8.0);
         B[d] = p->brick[d] ? p->brick[d] : (int)std::lround(cells * stride_hint / vol->sp[d]);
         B[d] = std::max(1, std::min(B[d], (int)std::min<int64_t>(vol->n[d], 224)));
         const double hf = p->halo_factor > 0.0f ? p->halo_factor : (vol->ndim == 3 ? 2.5 : 3.5);
@@ -1282,7 +1283,7 @@ extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_ev
         Gs.push_back(G);
     }
     std::vector<std::array<int, 3>> cells;
-    if (v0->ndim == 2) cells = {{8, 8, 1}, {12, 8, 1}, {16, 8, 1}, {16, 16, 1}};
+    if (v0->ndim == 2) cells = {{8, 8, 1}, {10, 8, 1}, {12, 8, 1}, {16, 8, 1}};
     else cells = {{2, 2, 2}, {2, 2, 1}, {3, 3, 2}, {4, 4, 2}};
 
     // trial copies of the contour states (trials must not move the real contours)

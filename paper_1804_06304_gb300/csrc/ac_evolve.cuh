@@ -277,6 +277,19 @@ __device__ __forceinline__ void add_terms(KSum *acc, const Terms &x, const Terms
     }
 }
 
+// Four samples (two Philox blocks in 2D) summed pairwise in two roundings, then
+// one compensated addition: fewer additions per sample than pair-wise steps.
+template <int DIM, bool COMP>
+__device__ __forceinline__ void add_terms4(KSum *acc, const Terms &x, const Terms &y, const Terms &z, const Terms &w)
+{
+#pragma unroll
+    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) {
+        const float s = (x.v[i] + y.v[i]) + (z.v[i] + w.v[i]);
+        if (COMP) kadd(acc[i], s);
+        else acc[i].s += s;
+    }
+}
+
 // All samples of one contour-iteration handled by this lane (lane `lig` of G).
 // 3D: sample j uses Philox block (j, n, k, stream): radius cbrt(u0), cos(phi) =
 // 1 - 2 u1, azimuth 2 pi u2.  2D: block m gives samples 2m and 2m+1, radius
@@ -340,11 +353,19 @@ __device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DI
             else add_terms<DIM, COMP>(acc, x);
         }
     } else {
-        // the two samples of a Philox block form a pair; an odd N leaves one sample
-        // of the last block, handled after the loop
+        // the two samples of a Philox block form a pair; two blocks of a lane (m and
+        // m + G) are summed together; a leftover block and an odd N's last sample
+        // are handled after the loop
         const int pairs = a.N >> 1;
+        int m = lig;
 #pragma unroll 1
-        for (int m = lig; m < pairs; m += G) {
+        for (; m + G < pairs; m += 2 * G) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
+            const uint4 u = philox4x32_10(make_uint4((uint32_t)(m + G), n, k, stream), a.rk0, a.rk1);
+            add_terms4<DIM, COMP>(acc, sample2<DIM, ACC>(gat, ic, a, w.x, w.y), sample2<DIM, ACC>(gat, ic, a, w.z, w.w),
+                                  sample2<DIM, ACC>(gat, ic, a, u.x, u.y), sample2<DIM, ACC>(gat, ic, a, u.z, u.w));
+        }
+        if (m < pairs) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
             add_terms<DIM, COMP>(acc, sample2<DIM, ACC>(gat, ic, a, w.x, w.y), sample2<DIM, ACC>(gat, ic, a, w.z, w.w));
         }
@@ -504,7 +525,9 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *keys, int64_t
 // the volume and the region), the clamped shared-memory path (ball crosses the
 // volume border) or, when the ball has left the region, global-memory gathers.
 template <int DIM, typename T, int G, bool COMP, bool ACC>
-__global__ void __maxnreg__(DIM == 2 ? 80 : 128) evolve_brick_kernel(const __grid_constant__ EvolveArgs a)
+// Register caps: 96 in 2D lets two 10-warp CTAs share an SM; 128 in 3D, two
+// 8-warp CTAs (or one of 16 warps).
+__global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __grid_constant__ EvolveArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
