@@ -248,6 +248,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 reference measurement")
     args = ap.parse_args(argv)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -377,6 +378,45 @@ def main(argv=None):
             "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
 
+    # the other roofs the path touches: HBM (the volume and the contour state per
+    # launch, measured copy bandwidth) and the shared-memory gathers (2D: one 8- or
+    # 16-byte quad per sample; 3D: eight taps), each as a fraction of its peak
+    other = None
+    if args.path != "grid":
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        hbm_alg = vol.nbytes + C.count * 20 * 2   # volume read once, state read and written
+        tap = 8 if (ndim == 2 and vol.dtype.itemsize <= 2 and vol.dtype != np.uint16) else \
+            16 if ndim == 2 else 8 * vol.dtype.itemsize
+        smem_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e9   # 32 banks x 4 B per clock per SM, GB/s
+        gb = tap * samples / (k_ms * 1e-3) / 1e9
+        other = {"hbm": {"achieved": hbm_alg / (k_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_alg / (k_ms * 1e-3) / 1e9 / hbm_peak,
+                         "note": "algorithmic bytes: volume once + contour state in and out, per evolve launch"},
+                 "smem_gather": {"achieved": gb, "peak": smem_peak, "unit": "GB/s", "frac": gb / smem_peak,
+                                 "bytes_per_sample": tap}}
+
+    # the reference point the metric names: the plain FP32 path (one launch per
+    # iteration, global gathers, plain FP32 sums) on the same workload
+    plain = None
+    if args.path == "brick" and not args.no_plain and not rules:
+        pp = dataclasses.replace(params, path=ac.AC_PATH_PLAIN, compensated=0, lanes_per_contour=0,
+                                 warps_per_block=0, brick=(0, 0, 0))
+        ac.ac_reseed(C)
+        ac.ac_evolve(C, pp)
+        torch.cuda.synchronize()
+        pms = []
+        for _ in range(max(3, min(args.steps, 5))):
+            flush.zero_()
+            ac.ac_reseed(C)
+            ac.ac_evolve(C, pp)
+            pms.append(ac.ac_evolve_kernel_ms(C))
+        p_ms, p_val = aggregate_ranks(pms, samples, world, reducer)
+        plain = {"value": p_val, "unit": "samples/s", "kernel_ms": p_ms,
+                 "speedup": (world * samples / (k_ms * 1e-3)) / p_val,
+                 "note": "evolve kernels only, both arms; plain path with plain FP32 sums"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.path != "grid":
         v, thr, desc = oracle_sample(s, vol, wl, spacing, args.cpu_seconds)
@@ -418,7 +458,8 @@ def main(argv=None):
             "cells": n_cells,
             "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
             "gpu_launches": int(launches),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roof, "other_roofs": other, "vs_plain_fp32": plain,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         }
         print(json.dumps(line))
     if dist_on:

@@ -641,3 +641,30 @@ def test_freeze_rule_stops_converged_contours_early(oracle):
     for i in range(len(seeds)):   # trace rows stop at the last evaluation, which is the final state
         assert np.isnan(tr[ne[i]:, i]).all() and not np.isnan(tr[:ne[i], i]).any()
         np.testing.assert_array_equal(tr[ne[i] - 1, i, :4], cR[i])
+
+
+def test_freeze_rule_counts_consecutive_steps(oracle):
+    """On a noisy image, where steps wander around the tolerance, a contour stops
+    exactly when freeze_iters consecutive proposed steps are small: the trace shows
+    freeze_iters - 1 small applied steps before the stop and no earlier run that
+    long, and contours that ran to T never had such a run."""
+    from paper_1804_06304_gb300 import synth
+    s = synth.small_3d(3)
+    img = oracle.VolumeImage(s.volume)
+    R0 = 4.0 / math.sqrt(1.5)
+    seeds = oracle.seed_lattice(3, s.shape_xyz, (1.0, 1.0, 1.0), 4.0)[::7]
+    kw = dict(eps0=8 * R0**2 / s.contrast, max_step=0.5, Rmin=R0 / 2, Rmax=3 * R0, seed=6)
+    tol, k = 0.12, 3
+    cR, E, tr, st, ne = oracle.evolve(img, oracle.make_params(3, 64, 60, freeze_tol=tol, freeze_iters=k, **kw),
+                                      seeds, trace=True, stops=True)
+    assert 0 < (st == 1).sum() < len(seeds)
+    for i in range(len(seeds)):
+        rows = tr[:ne[i], i, :4]
+        step = np.abs(np.diff(rows, axis=0)).max(axis=1)
+        run, longest = 0, 0
+        for small in step < tol:
+            run = run + 1 if small else 0
+            longest = max(longest, run)
+        assert longest < k
+        if st[i] == 1:
+            assert run == k - 1, (i, step[-k:])
