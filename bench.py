@@ -336,6 +336,8 @@ def main(argv=None):
         ev1[i].record()
         kernel_ms.append(ac.ac_evolve_kernel_ms(C))
         n_cells = len(cells)
+    from paper_1804_06304_gb300.evaluate import detection_prf
+    detection = detection_prf(cells["c"][:, :ndim], s.centres[:, :ndim], s.radii)
     torch.cuda.synchronize()
     launches = ac.ac_kernel_launches() - launches0
     paths = ac.ac_evolve_stats(C)
@@ -436,6 +438,7 @@ def main(argv=None):
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "contour_iterations_per_s": gval, "evolve_kernel_ms": k_ms,
             "evolve_contour_iterations_per_s": world * citers / (k_ms * 1e-3), "cells": n_cells,
+            "detection": detection,
             "gpu_launches": int(launches), "roofline": None, "cpu_baseline": None,
             "e2e": None if e2e is None else dict(e2e, value=e2e["value"] / wl["N"], unit="contour-iterations/s"),
             "clocks": clk}))
@@ -456,6 +459,7 @@ def main(argv=None):
             "evaluated_contour_iterations": int(sum(paths)),
             "stopped": dict(zip(("freeze", "cull"), ac.ac_evolve_stops(C))) if rules else None,
             "cells": n_cells,
+            "detection": detection,
             "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
             "gpu_launches": int(launches),
             "roofline": roof, "other_roofs": other, "vs_plain_fp32": plain,
@@ -493,14 +497,20 @@ def batch_arm(args, wl, rank, world, dev):
     total = sum(c.count for c in C)
     samples = total * wl["N"] * wl["T"]
 
-    def step(from_host=False):
+    def step(from_host=False, keep=None):
         if from_host:
             for v, src in zip(V, pinned):
                 ac.ac_load_volume(v, src)
         for c in C:
             ac.ac_reseed(c)
         ac.ac_plan_launch(plan, use_graph=True)
-        return sum(len(ac.ac_localize(c, E0)) for c in C)
+        n = 0
+        for i, c in enumerate(C):
+            cells = ac.ac_localize(c, E0)
+            n += len(cells)
+            if keep is not None:
+                keep.append(cells)
+        return n
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -530,6 +540,14 @@ def batch_arm(args, wl, rank, world, dev):
     reducer = torch_max_reducer(dev) if dist_on else None
     t_ms, value = aggregate_ranks(ms, samples, world, reducer)
     k_ms, _ = aggregate_ranks(kms, samples, world, reducer)
+    from paper_1804_06304_gb300.evaluate import match_inside
+    kept = []
+    step(keep=kept)
+    tp = sum(match_inside(c["c"], sv.centres, sv.radii) for c, sv in zip(kept, vols))
+    n_det, n_true = sum(len(c) for c in kept), sum(len(sv.centres) for sv in vols)
+    pr, rc = tp / max(n_det, 1), tp / max(n_true, 1)
+    detection = {"tp": tp, "fp": n_det - tp, "fn": n_true - tp, "precision": pr, "recall": rc,
+                 "f": 2 * pr * rc / (pr + rc) if pr + rc > 0 else 0.0}
     e2e = None
     if not args.no_e2e:
         ems = []
@@ -563,7 +581,8 @@ def batch_arm(args, wl, rank, world, dev):
                        "autotuned": {"lanes_per_contour": params.lanes_per_contour, "brick": list(params.brick),
                                      "warps_per_block": params.warps_per_block, "seconds": tune_s},
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-            "cells": cells, "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
+            "cells": cells, "detection": detection,
+            "gather_paths": {"fast": paths[0], "clamped": paths[1], "global": paths[2]},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "evolve_brick_kernel (plan, graph)",

@@ -1,9 +1,10 @@
 """Thin ctypes binding of libac (include/ac.h), with the C ABI's names.
 
 Argument marshalling only: every step of the method runs in the CUDA library.
-Importing this module loads (and, if needed, builds) ``libac.so``; when the
-library cannot be built or loaded the import fails loudly -- there is no CPU
-path.  Arrays may be numpy (host) or torch tensors (host or CUDA).
+``load()`` builds (if stale) and loads ``libac.so``; when the library cannot be
+built or loaded it fails loudly -- there is no CPU path.  With the environment
+variable ``AC_BUILD=checked`` the bounds-checked build is loaded instead.  Arrays
+may be numpy (host) or torch tensors (host or CUDA).
 """
 from __future__ import annotations
 
@@ -130,15 +131,22 @@ _SIGS = {
 _lib = None
 
 
+def _checked() -> bool:
+    v = os.environ.get("AC_BUILD", "")
+    if v not in ("", "checked"):
+        raise ACError(AC_ERR_ARG, f"AC_BUILD must be unset or 'checked', not {v!r}")
+    return v == "checked"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.lib_path(_checked())
 
 
 def load():
     """Build (if stale) and load libac.so; raises if either fails."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(checked=_checked())
         l = ct.CDLL(path)
         for name, (res, args) in _SIGS.items():
             f = getattr(l, name)

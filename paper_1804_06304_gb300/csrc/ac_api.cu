@@ -84,6 +84,7 @@ extern "C" ac_status ac_create_volume(const void *data, int data_on_device, ac_d
                                       const float spacing[3], float intensity_scale, void *cuda_stream,
                                       ac_volume **out)
 {
+    ac::Range nvtx_range("ac_create_volume");
     g_err.clear();
     if (!out) AC_FAIL(AC_ERR_ARG, "ac_create_volume: out is NULL");
     *out = nullptr;
@@ -138,6 +139,7 @@ extern "C" ac_status ac_create_volume(const void *data, int data_on_device, ac_d
 extern "C" ac_status ac_load_volume(ac_volume *vol, const void *data, int data_on_device, int64_t row_stride,
                                     int64_t plane_stride, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_load_volume");
     g_err.clear();
     if (!vol || !data) AC_FAIL(AC_ERR_ARG, "ac_load_volume: NULL argument");
     if (row_stride == 0) row_stride = vol->n[0];
@@ -197,6 +199,7 @@ static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out)
 extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const float *explicit_cR,
                              int64_t n_explicit, void *cuda_stream, ac_contours **out)
 {
+    ac::Range nvtx_range("ac_seed");
     g_err.clear();
     if (!out) AC_FAIL(AC_ERR_ARG, "ac_seed: out is NULL");
     *out = nullptr;
@@ -270,6 +273,7 @@ extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const
 
 extern "C" ac_status ac_reseed(ac_contours *c, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_reseed");
     if (!c) AC_FAIL(AC_ERR_ARG, "ac_reseed: NULL handle");
     if (!c->lattice) AC_FAIL(AC_ERR_STATE, "ac_reseed: handle was seeded explicitly");
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -310,6 +314,8 @@ static ac_status check_status(ac_contours *ctr, cudaStream_t st)
     if (s[0] & STATUS_TMA_TIMEOUT) AC_FAIL(AC_ERR_TIMEOUT, "device status: a brick load did not complete in time");
     if (s[0] & STATUS_LOCALIZE_LIMIT) AC_FAIL(AC_ERR_TIMEOUT, "device status: localization round bound reached");
     if (s[0] & STATUS_NONFINITE) AC_FAIL(AC_ERR_NUMERIC, "device status: non-finite contour state");
+    if (s[0] & STATUS_BOUNDS)
+        AC_FAIL(AC_ERR_STATE, "device status: a gather index left its array (bounds-checked build)");
     if (s[0] & STATUS_GRID_RANGE)
         AC_FAIL(AC_ERR_ARG, "device status: a contour radius exceeded the grid path's bound (contour stopped)");
     return AC_OK;
@@ -923,6 +929,7 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
                                       float intensity_scale, float *state_dev, int64_t n_contours, float r0,
                                       float stride, const ac_evolve_params *p, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_evolve_static");
     g_err.clear();
     if (n_contours > AC_STATIC_MAX_CONTOURS)
         AC_FAIL(AC_ERR_BUDGET, "ac_evolve_static: n_contours exceeds AC_STATIC_MAX_CONTOURS (" +
@@ -1128,6 +1135,7 @@ static void drop_graph(ac_plan *pl)
 extern "C" ac_status ac_plan_create(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
                                     const ac_evolve_params *params, ac_plan **out)
 {
+    ac::Range nvtx_range("ac_plan_create");
     g_err.clear();
     if (!out) AC_FAIL(AC_ERR_ARG, "ac_plan_create: out is NULL");
     *out = nullptr;
@@ -1153,6 +1161,7 @@ extern "C" ac_status ac_plan_create(ac_contours *const *sets, const ac_batch_ite
 extern "C" ac_status ac_plan_rebind(ac_plan *pl, ac_contours *const *sets, const ac_batch_item *items,
                                     int32_t n_sets, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_plan_rebind");
     g_err.clear();
     if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_rebind: NULL plan");
     if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_plan_rebind: need 1..4096 sets");
@@ -1186,6 +1195,7 @@ extern "C" ac_status ac_plan_set_items(ac_plan *pl, const ac_batch_item *items, 
 
 extern "C" ac_status ac_plan_launch(ac_plan *pl, int use_graph, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_plan_launch");
     g_err.clear();
     if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_launch: NULL plan");
     if (!pl->valid) AC_FAIL(AC_ERR_STATE, "ac_plan_launch: the plan has no sets (a rebind failed)");
@@ -1246,6 +1256,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_evolve_params *params, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_autotune");
     g_err.clear();
     if (!sets || n_sets < 1 || n_sets > 4096 || !params) AC_FAIL(AC_ERR_ARG, "ac_autotune: need 1..4096 sets and params");
     ac_status s = check_params(params);
@@ -1378,6 +1389,7 @@ extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_ev
 extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params, const ac_trace *trace,
                                void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_evolve");
     g_err.clear();
     if (!ctr) AC_FAIL(AC_ERR_ARG, "ac_evolve: ctr is NULL");
     return evolve_sets(&ctr, nullptr, 1, params, trace, (cudaStream_t)cuda_stream);
@@ -1386,6 +1398,7 @@ extern "C" ac_status ac_evolve(ac_contours *ctr, const ac_evolve_params *params,
 extern "C" ac_status ac_evolve_batch(ac_contours *const *sets, const ac_batch_item *items, int32_t n_sets,
                                      const ac_evolve_params *params, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_evolve_batch");
     g_err.clear();
     if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_evolve_batch: need 1..4096 sets");
     return evolve_sets(sets, items, n_sets, params, nullptr, (cudaStream_t)cuda_stream);
@@ -1455,6 +1468,7 @@ extern "C" ac_status ac_evolve_kernel_ms(ac_contours *ctr, float *ms)
 extern "C" ac_status ac_localize(ac_contours *ctr, const ac_localize_params *params, ac_cell *out_host, int64_t cap,
                                  int64_t *n_out, void *cuda_stream)
 {
+    ac::Range nvtx_range("ac_localize");
     g_err.clear();
     if (!ctr || !params || !n_out || cap < 0 || (cap > 0 && !out_host)) AC_FAIL(AC_ERR_ARG, "ac_localize: bad arguments");
     if (std::isnan(params->E0)) AC_FAIL(AC_ERR_ARG, "ac_localize: E0 is NaN");

@@ -142,13 +142,15 @@ template <typename QT> struct QuadFast {
     const QT *Q;
     int qp;          // quads per row
     float M[2];
+    int nq;          // quads in the region (checked build)
+    int32_t *st;     // status word (checked build)
     __device__ __forceinline__ float at(float x0, float x1, float) const
     {
         int i0, i1;
         float f0, f1;
         fast_axis(x0, M[0], i0, f0);
         fast_axis(x1, M[1], i1, f1);
-        return quad_lerp(quad_f(Q[i1 * qp + i0]), f0, f1);
+        return quad_lerp(quad_f(Q[checked(i1 * qp + i0, nq, st)]), f0, f1);
     }
 };
 
@@ -167,17 +169,40 @@ __device__ __forceinline__ float interp(const T *q, int64_t py, int64_t pz, floa
     return fmaf(f2, s1 - s0, s0);
 }
 
+// Tap loaders; base, n and st serve the checked build only.
 template <typename T> struct SmemLoad {
-    __device__ __forceinline__ float operator()(const T *p) const { return to_f<T>(*p); }
+    const T *base;
+    int64_t n;
+    int32_t *st;
+    __device__ __forceinline__ float operator()(const T *p) const
+    {
+#ifdef AC_CHECKED
+        return to_f<T>(base[checked((int64_t)(p - base), n, st)]);
+#else
+        return to_f<T>(*p);
+#endif
+    }
 };
 template <typename T> struct GlobalLoad {
-    __device__ __forceinline__ float operator()(const T *p) const { return ldg_f<T>(p); }
+    const T *base;
+    int64_t n;
+    int32_t *st;
+    __device__ __forceinline__ float operator()(const T *p) const
+    {
+#ifdef AC_CHECKED
+        return ldg_f<T>(base + checked((int64_t)(p - base), n, st));
+#else
+        return ldg_f<T>(p);
+#endif
+    }
 };
 
 template <int DIM, typename T> struct RawFast {
     const T *p;
     int py, pz;
     float M[3];
+    int64_t n;       // voxels in the region (checked build)
+    int32_t *st;
     __device__ __forceinline__ float at(float x0, float x1, float x2) const
     {
         int i0, i1, i2 = 0;
@@ -185,7 +210,7 @@ template <int DIM, typename T> struct RawFast {
         fast_axis(x0, M[0], i0, f0);
         fast_axis(x1, M[1], i1, f1);
         if (DIM == 3) fast_axis(x2, M[2], i2, f2);
-        return interp<DIM, T>(p + i0 + i1 * py + i2 * pz, py, pz, f0, f1, f2, SmemLoad<T>());
+        return interp<DIM, T>(p + i0 + i1 * py + i2 * pz, py, pz, f0, f1, f2, SmemLoad<T>{p, n, st});
     }
 };
 
@@ -195,6 +220,8 @@ template <int DIM, typename T, bool QUAD> struct SmemClamp {
     int py, pz;      // raw pitches, or quads per row in py
     AxisSplit ax[3];
     int o[3];        // centre voxel relative to the region origin
+    int64_t n;       // quads or voxels in the region (checked build)
+    int32_t *st;
     __device__ __forceinline__ float at(float x0, float x1, float x2) const
     {
         int b0, b1, b2 = 0;
@@ -204,10 +231,11 @@ template <int DIM, typename T, bool QUAD> struct SmemClamp {
         if (DIM == 3) axis_tap(ax[2], x2, b2, f2);
         if (QUAD) {
             using QT = typename QuadOf<T>::type;
-            return quad_lerp(quad_f(reinterpret_cast<const QT *>(p)[(o[1] + b1) * py + (o[0] + b0)]), f0, f1);
+            const int64_t qi = checked((int64_t)(o[1] + b1) * py + (o[0] + b0), n, st);
+            return quad_lerp(quad_f(reinterpret_cast<const QT *>(p)[qi]), f0, f1);
         }
         const T *q = reinterpret_cast<const T *>(p) + (o[0] + b0) + (o[1] + b1) * py + (DIM == 3 ? (o[2] + b2) * pz : 0);
-        return interp<DIM, T>(q, py, pz, f0, f1, f2, SmemLoad<T>());
+        return interp<DIM, T>(q, py, pz, f0, f1, f2, SmemLoad<T>{reinterpret_cast<const T *>(p), n, st});
     }
 };
 
@@ -216,6 +244,8 @@ template <int DIM, typename T> struct GlobalClamp {
     const T *p;
     int64_t py, pz;
     AxisSplit ax[3];
+    int64_t n;       // elements of the row-pitched volume (checked build)
+    int32_t *st;
     __device__ __forceinline__ float at(float x0, float x1, float x2) const
     {
         int b0, b1, b2 = 0;
@@ -225,7 +255,7 @@ template <int DIM, typename T> struct GlobalClamp {
         if (DIM == 3) axis_tap(ax[2], x2, b2, f2);
         const T *q = p + (int64_t)(ax[0].ci + b0) + (int64_t)(ax[1].ci + b1) * py +
                      (DIM == 3 ? (int64_t)(ax[2].ci + b2) * pz : 0);
-        return interp<DIM, T>(q, py, pz, f0, f1, f2, GlobalLoad<T>());
+        return interp<DIM, T>(q, py, pz, f0, f1, f2, GlobalLoad<T>{p, n, st});
     }
 };
 
@@ -576,6 +606,8 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
     }
 
     const int py = a.ext[0], pz = a.ext[0] * a.ext[1];
+    const int nquads = qp * (a.ext[1] - 1);                       // extents for the checked build
+    const int64_t nraw = (int64_t)a.ext[0] * a.ext[1] * a.ext[2];
     const int lig = threadIdx.x % G;
     const int grp = threadIdx.x / G;
     const int ngrp = blockDim.x / G;
@@ -614,23 +646,25 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
             if (inside && interior) {
                 const float M[3] = {8388608.0f + (float)o[0], 8388608.0f + (float)o[1], 8388608.0f + (float)o[2]};
                 if (quad) {
-                    QuadFast<QT> gat{Q, qp, {M[0], M[1]}};
+                    QuadFast<QT> gat{Q, qp, {M[0], M[1]}, nquads, V.status};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 } else {
-                    RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}};
+                    RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}, nraw, V.status};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 }
             } else if (inside) {
                 if (quad) {
-                    SmemClamp<DIM, T, true> gat{Q, qp, 0, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]}};
+                    SmemClamp<DIM, T, true> gat{Q, qp, 0, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]},
+                                                nquads, V.status};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 } else {
-                    SmemClamp<DIM, T, false> gat{reg, py, pz, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]}};
+                    SmemClamp<DIM, T, false> gat{reg, py, pz, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]},
+                                                 nraw, V.status};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 }
             } else {
                 GlobalClamp<DIM, T> gat{reinterpret_cast<const T *>(V.data), V.pitch_y, V.pitch_z,
-                                        {ic.ax[0], ic.ax[1], ic.ax[2]}};
+                                        {ic.ax[0], ic.ax[1], ic.ax[2]}, V.pitch_z * V.n[2], V.status};
                 s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
             }
             if (lig == 0) write_trace(a, v, k, n, c, R, s);
@@ -684,7 +718,7 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
         IterC<DIM> ic;
         iter_consts<DIM>(ic, c, R, V, a);
         GlobalClamp<DIM, T> gat{reinterpret_cast<const T *>(V.data), V.pitch_y, V.pitch_z,
-                                {ic.ax[0], ic.ax[1], ic.ax[2]}};
+                                {ic.ax[0], ic.ax[1], ic.ax[2]}, V.pitch_z * V.n[2], V.status};
         const Step s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
         if (lig == 0) {
             ++glob;

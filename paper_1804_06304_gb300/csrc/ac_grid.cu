@@ -30,6 +30,7 @@ __device__ __forceinline__ Step eval_grid(const VolDesc &V, const EvolveArgs &a,
     const float B1 = fmaf(-a.rho * R, a.inv_dr, 0.5f);   // inner band coordinate: r / dr + B1
     const float B2 = fmaf(-R, a.inv_dR, 0.5f);           // outer band coordinate: r / dR + B2
     const T *data = reinterpret_cast<const T *>(V.data);
+    const int64_t nvox = V.pitch_z * V.n[2];   // extent for the checked build
     KSum acc[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int kz = lo[2]; kz <= hi[2]; ++kz) {
         const float dz = DIM == 3 ? fmaf((float)kz, V.sp[2], -c[2]) : 0.0f;
@@ -42,10 +43,10 @@ __device__ __forceinline__ Step eval_grid(const VolDesc &V, const EvolveArgs &a,
             const int i0 = (int)ceilf((c[0] - chord) * V.inv_sp[0]);
             const int i1 = (int)floorf((c[0] + chord) * V.inv_sp[0]);
             const int yy = min(max(jy, 0), V.n[1] - 1);
-            const T *row = data + (int64_t)zz * V.pitch_z + (int64_t)yy * V.pitch_y;
+            const int64_t row = (int64_t)zz * V.pitch_z + (int64_t)yy * V.pitch_y;
             for (int ix = i0 + lig; ix <= i1; ix += G) {
                 const float dx = fmaf((float)ix, V.sp[0], -c[0]);
-                const float I = ldg_f<T>(row + min(max(ix, 0), V.n[0] - 1));
+                const float I = ldg_f<T>(data + checked(row + min(max(ix, 0), V.n[0] - 1), nvox, V.status));
                 const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 const float t1 = fmaf(r, a.inv_dr, B1), t2 = fmaf(r, a.inv_dR, B2);
                 const float r1 = __saturatef(t1), r2 = __saturatef(t2);

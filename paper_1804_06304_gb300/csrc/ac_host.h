@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "ac_internal.cuh"
@@ -79,6 +81,15 @@ namespace ac {
 
 // thread-local error message
 void set_error(const std::string &msg);
+
+// NVTX range for the lifetime of a scope (visible in profilers' timelines; a no-op
+// when no tool is attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 // count of the library's own kernel launches
 void count_launch(int64_t n = 1);
 

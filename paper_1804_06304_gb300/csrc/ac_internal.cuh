@@ -16,8 +16,26 @@ enum : int32_t {
     STATUS_TMA_TIMEOUT = 1,   // a brick's TMA load did not complete within the bound
     STATUS_NONFINITE = 2,     // a contour's state or energy became non-finite
     STATUS_LOCALIZE_LIMIT = 4,// localization rounds hit their bound
-    STATUS_GRID_RANGE = 8     // grid path: a ball wider than the grid bound (contour stopped)
+    STATUS_GRID_RANGE = 8,    // grid path: a ball wider than the grid bound (contour stopped)
+    STATUS_BOUNDS = 16        // checked build: a gather index outside its array (read as 0, reported)
 };
+
+// Checked build (compiled with AC_CHECKED): every gather index is tested against
+// the extent of the array it reads; an index outside reads element 0 instead and
+// sets STATUS_BOUNDS in the set's status word.  Otherwise the identity.
+template <typename I> __device__ __forceinline__ I checked(I i, I n, int32_t *st)
+{
+#ifdef AC_CHECKED
+    if (i < 0 || i >= n) {
+        atomicOr(st, STATUS_BOUNDS);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)st;
+#endif
+    return i;
+}
 
 // Grid path: largest ball radius, in voxels along any axis, that an evaluation
 // may cover (bounds the work of one evaluation).

@@ -157,6 +157,7 @@ void serve_loop(ac_server *S)
         if (S->resident.empty()) continue;
 
         // one round: every resident tile advances up to iters_per_round iterations
+        ac::Range nvtx_round("ac_server_round");
         const int n = (int)S->resident.size();
         std::vector<ac_contours *> sets(n);
         std::vector<ac_batch_item> items(n);

@@ -1,0 +1,38 @@
+"""The bounds-checked build (AC_BUILD=checked; -DAC_CHECKED: every gather index is
+tested against its array) runs every gather of tests/_checked_cases.py without a
+bounds report, and its results agree with the normal build's to rounding (the added
+index tests can change how the compiler contracts floating-point expressions; most
+cases come out bit-identical).  This stands in for compute-sanitizer, which is not
+available on these machines."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_checked_build_matches_and_stays_in_bounds(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from tests._checked_cases import run_cases
+    normal = run_cases()
+    out = tmp_path / "checked.npz"
+    env = dict(os.environ, AC_BUILD="checked")
+    r = subprocess.run([sys.executable, "-m", "tests._checked_cases", str(out)], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=1800)
+    # an index outside its array would surface as AC_ERR_STATE at the child's first synchronizing call
+    assert r.returncode == 0, r.stderr[-3000:]
+    checked = np.load(out)
+    assert sorted(checked.files) == sorted(normal)
+    assert normal["b3_global_paths"][2] > 0          # the global-memory fallback was exercised
+    same = 0
+    for k in normal:
+        np.testing.assert_allclose(checked[k], normal[k], rtol=1e-5, atol=1e-5, err_msg=k)
+        same += int(np.array_equal(checked[k], normal[k]))
+    print("CHECKED_BITWISE_EQUAL", same, "of", len(normal))
