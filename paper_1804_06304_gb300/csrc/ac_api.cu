@@ -25,7 +25,7 @@ void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed
 
 void Scratch::release_all()
 {
-    DevBuf *all[] = {&keys, &vals, &skeys, &svals, &cub, &desc, &tmaps, &flags, &surv, &ekeys, &surv_sorted,
+    DevBuf *all[] = {&keys, &vals, &skeys, &svals, &cub, &desc, &tmaps, &active, &flags, &surv, &ekeys, &surv_sorted,
                      &pos, &cellk, &celli, &cellk_s, &celli_s, &cell_start, &stat, &acc, &cells, &counters};
     for (DevBuf *b : all) b->release();
 }
@@ -626,7 +626,52 @@ struct Prepared {
     std::vector<VolDesc> desc;
     std::vector<CUtensorMap> maps;
     ac_contours *owner = nullptr;   // status word, path counters, kernel-time events
+    // brick launches with an energy rule inside the span run in two phases: the
+    // brick kernel up to cull_iter, then the plain kernel over the contours still
+    // running (compacted); desc2 holds the second phase's windows
+    bool split = false;
+    int32_t p2_first = 0, p2_last = -1;
+    std::vector<VolDesc> desc2;
 };
+
+// Phase windows of a split launch (see Prepared::split) and the upload of the
+// descriptors: [phase-1 or only descriptors | phase-2 descriptors].
+ac_status upload_desc(Prepared &pr, Scratch &sc, cudaStream_t st)
+{
+    const EvolveArgs &a = pr.a;
+    const int c = a.cull_iter;
+    pr.split = pr.pl.brick && c > 0 && c >= a.first_iter && c < a.last_iter;
+    std::vector<VolDesc> d1 = pr.desc;
+    if (pr.split) {
+        pr.desc2 = pr.desc;
+        pr.p2_first = c + 1;
+        pr.p2_last = a.last_iter;
+        for (int i = 0; i < pr.n_sets; ++i) {
+            const VolDesc &o = pr.desc[i];
+            VolDesc &x = d1[i], &y = pr.desc2[i];
+            if (o.first_iter > o.last_iter) continue;   // empty window stays empty in both
+            if (o.first_iter > c) {                     // entirely after the energy test
+                x.first_iter = 1;
+                x.last_iter = 0;
+            } else {
+                x.last_iter = std::min(o.last_iter, c);
+                x.update_last = o.last_iter > c ? 1 : o.update_last;
+            }
+            if (o.last_iter <= c) {                     // entirely up to the energy test
+                y.first_iter = 1;
+                y.last_iter = 0;
+            } else {
+                y.first_iter = std::max(o.first_iter, c + 1);
+            }
+        }
+    }
+    AC_CUDA(sc.desc.ensure(sizeof(VolDesc) * pr.n_sets * 2));
+    AC_CUDA(cudaMemcpyAsync(sc.desc.p, d1.data(), sizeof(VolDesc) * pr.n_sets, cudaMemcpyHostToDevice, st));
+    if (pr.split)
+        AC_CUDA(cudaMemcpyAsync(sc.desc.as<VolDesc>() + pr.n_sets, pr.desc2.data(), sizeof(VolDesc) * pr.n_sets,
+                                cudaMemcpyHostToDevice, st));
+    return AC_OK;
+}
 
 // Applies per-set iteration windows and stream words to the descriptors and the
 // launch's iteration span.
@@ -766,9 +811,12 @@ ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int
     }
     if (total == 0) return AC_OK;
 
-    AC_CUDA(sc.desc.ensure(sizeof(VolDesc) * n_sets));
-    AC_CUDA(cudaMemcpyAsync(sc.desc.p, pr.desc.data(), sizeof(VolDesc) * n_sets, cudaMemcpyHostToDevice, st));
+    s = upload_desc(pr, sc, st);
+    if (s != AC_OK) return s;
     a.vols = sc.desc.as<VolDesc>();
+    // the compaction list exists whenever a split is possible, so its address is
+    // fixed for every later item change of a plan
+    if (pl.brick && a.cull_iter > 0) AC_CUDA(sc.active.ensure(sizeof(uint32_t) * total + 64));
     if (!sets[0]->ev0) {
         AC_CUDA(cudaEventCreate(&sets[0]->ev0));
         AC_CUDA(cudaEventCreate(&sets[0]->ev1));
@@ -820,6 +868,30 @@ ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int
     return AC_OK;
 }
 
+// Contours whose second-phase window is not empty and that no rule has stopped,
+// appended (in any order: every contour evolves independently) to `list`.
+__global__ void compact_active_kernel(const VolDesc *vols, int n_vols, int64_t total, uint32_t *list,
+                                      unsigned long long *count)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += stride) {
+        int v = 0;
+        for (int i = 1; i < n_vols; ++i)
+            if (vols[i].contour_base <= gi) v = i;
+        const VolDesc &V = vols[v];
+        const int64_t k = gi - V.contour_base;
+        const bool run = V.first_iter <= V.last_iter && !(V.hold && (V.hold[k] & HOLD_STOPPED));
+        // one atomic per warp: the lanes of this iteration share a block of the list
+        const unsigned act = __activemask();
+        const unsigned m = __ballot_sync(act, run);
+        const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+        unsigned long long base = 0;
+        if (lane == leader && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(act, base, leader);
+        if (run) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)gi;
+    }
+}
+
 // Device work of a prepared launch only (no host synchronisation, no allocation):
 // counters, binning by brick, sort, evolution kernel(s), kernel-time events.
 // While a stream is captured, the kernel-time events become event-record nodes of
@@ -867,6 +939,34 @@ ac_status enqueue_prepared(Prepared &pr, Scratch &sc, cudaStream_t st, int64_t *
         cudaError_t e = launch_evolve(pr.dtype, a, pr.pl, pr.bricks, st);
         if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: brick launch: ") + cudaGetErrorString(e));
         ++nl;
+        if (pr.split) {
+            // second phase: the contours the energy rule left running, compacted,
+            // one plain launch per remaining iteration over a fixed grid that reads
+            // the list length on the device (no host synchronisation)
+            EvolveArgs b = a;
+            b.vols = sc.desc.as<VolDesc>() + pr.n_sets;
+            uint32_t *list = sc.active.as<uint32_t>();
+            unsigned long long *cnt = reinterpret_cast<unsigned long long *>(
+                reinterpret_cast<unsigned char *>(sc.active.p) + ((sizeof(uint32_t) * pr.total + 7) / 8 * 8));
+            AC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+            const int64_t cblocks = std::min<int64_t>((pr.total + 255) / 256, 1 << 16);
+            compact_active_kernel<<<(unsigned)cblocks, 256, 0, st>>>(b.vols, pr.n_sets, pr.total, list, cnt);
+            ++nl;
+            AC_CUDA(cudaGetLastError());
+            b.active = list;
+            b.n_active = cnt;
+            Plan p2 = pr.pl;
+            p2.brick = false;
+            p2.warps = std::min(p2.warps, 8);
+            const int64_t per_cta = (int64_t)p2.warps * 32 / p2.G;
+            const int64_t grid = std::min<int64_t>((pr.total + per_cta - 1) / per_cta, 152 * 16);
+            for (int n = pr.p2_first; n <= pr.p2_last; ++n) {
+                b.iter0 = n;
+                e = launch_evolve(pr.dtype, b, p2, grid, st);
+                if (e != cudaSuccess) AC_FAIL(AC_ERR_CUDA, std::string("ac_evolve: compacted launch: ") + cudaGetErrorString(e));
+                ++nl;
+            }
+        }
         AC_CUDA(cudaEventRecordWithFlags(owner->ev1, st, ev_flags));
     }
     owner->timed = true;
@@ -1185,11 +1285,15 @@ extern "C" ac_status ac_plan_set_items(ac_plan *pl, const ac_batch_item *items, 
     ac_status s = apply_items(pl->pr, items, &pl->params);
     if (s != AC_OK) return s;
     if (pl->pr.total == 0) return AC_OK;
-    AC_CUDA(cudaMemcpyAsync(pl->sc.desc.p, pl->pr.desc.data(), sizeof(VolDesc) * pl->pr.n_sets,
-                            cudaMemcpyHostToDevice, (cudaStream_t)cuda_stream));
-    // a captured plain-path graph holds one launch per iteration of its span
-    if (!pl->pr.pl.brick && !pl->pr.pl.grid && (pl->pr.a.first_iter != pl->span0 || pl->pr.a.last_iter != pl->span1))
-        drop_graph(pl);
+    Prepared &pr = pl->pr;
+    const bool was_split = pr.split;
+    const int32_t p2f = pr.p2_first, p2l = pr.p2_last;
+    s = upload_desc(pr, pl->sc, (cudaStream_t)cuda_stream);
+    if (s != AC_OK) return s;
+    // a captured graph holds one plain launch per iteration of its span (plain path,
+    // or the second phase of a split brick launch)
+    if (!pr.pl.brick && !pr.pl.grid && (pr.a.first_iter != pl->span0 || pr.a.last_iter != pl->span1)) drop_graph(pl);
+    if (pr.pl.brick && (was_split != pr.split || p2f != pr.p2_first || p2l != pr.p2_last)) drop_graph(pl);
     return AC_OK;
 }
 

@@ -705,7 +705,11 @@ __global__ void __launch_bounds__(256) evolve_plain_kernel(const __grid_constant
     const unsigned mask = group_mask<G>();
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     const int n = a.iter0;
-    for (int64_t gi = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G; gi < a.total_contours; gi += groups) {
+    // every contour, or only those of a compacted list (contours still running after
+    // a stopping rule)
+    const int64_t items = a.active ? (int64_t)*a.n_active : a.total_contours;
+    for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G; it < items; it += groups) {
+        const int64_t gi = a.active ? (int64_t)a.active[it] : it;
         const int v = find_vol(a, gi, false);
         const VolDesc &V = a.vols[v];
         if (n < V.first_iter || n > V.last_iter) continue;   // outside this set's iterations

@@ -51,7 +51,7 @@ struct DevBuf {
 };
 
 struct Scratch {
-    DevBuf keys, vals, skeys, svals, cub, desc, tmaps;               // evolve
+    DevBuf keys, vals, skeys, svals, cub, desc, tmaps, active;       // evolve
     DevBuf flags, surv, ekeys, surv_sorted, pos, cellk, celli, cellk_s, celli_s, cell_start, stat, acc,
         cells, counters;                                               // localize
     void release_all();

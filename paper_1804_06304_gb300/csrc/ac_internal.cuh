@@ -112,6 +112,8 @@ struct EvolveArgs {
     int64_t tk0, tk1;
     int32_t tt0, tt1;
     unsigned long long *path_counts;   // [3]: fast, clamped, global contour-iterations
+    const uint32_t *active;            // plain path: contours to visit (nullptr: all)
+    const unsigned long long *n_active;// device count of `active`
 };
 
 // ----------------------------------------------------------------- Philox4x32-10

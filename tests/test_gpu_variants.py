@@ -253,3 +253,22 @@ def test_stopping_rules_against_free_running_oracle(ac, oracle, small3d):
     same = (stop_gpu == stops) & (n_gpu == ne)
     dc = np.linalg.norm(r["final"][:3].T - cR[:, :3], axis=1)
     assert np.mean(dc[same] < 0.25) >= 0.99
+
+
+def test_split_launch_with_items_equals_plain(ac, small3d):
+    """An energy rule inside a brick launch splits it (brick kernel up to cull_iter,
+    then the plain kernel over the compacted survivors); per-set windows that
+    straddle, precede or follow cull_iter give exactly the plain path's results."""
+    s = small3d
+    E0 = ac.default_E0(3, s.contrast)
+    p = _p3(ac, s, T=10, cull_iter=6, cull_E=0.3 * E0)
+    items = [(1, 1, 10, 0), (2, 1, 5, 1), (3, 7, 4, 0)]   # straddles 6; ends before it; starts after it
+    V = ac.ac_create_volume(s.volume, s.spacing)
+    res = {}
+    for path in (ac.AC_PATH_BRICK, ac.AC_PATH_PLAIN):
+        sets = [ac.ac_seed(V, stride=st) for st in (4.0, 4.0, 5.0)]
+        ac.ac_evolve_batch(sets, dataclasses.replace(p, path=path), items=items)
+        res[path] = [ac.ac_get_state(c) for c in sets] + [np.array(ac.ac_evolve_stops(c)) for c in sets]
+    for x, y in zip(res[ac.AC_PATH_BRICK], res[ac.AC_PATH_PLAIN]):
+        np.testing.assert_array_equal(x, y)
+    assert res[ac.AC_PATH_BRICK][3][1] > 0   # the first set had contours culled
