@@ -70,11 +70,12 @@ WORKLOADS = {
                           "r 3-8; stride-4 lattices; one autotuned plan over all volumes replayed as a CUDA graph; "
                           "256 samples, 80 iterations"),
     "serve-3d": dict(ndim=3, stride=6.0, N=512, T=100, seed=4, tiles=8, requests=32, load=0.7, ipr=10,
-                     budget_gb=120,
+                     budget_gb=120, contour_cap=262144,
                      desc="request loop over uint16 tiles 128^3..1024x1024x64 (log-uniform voxel count, brain-3d "
                           "nucleus model, 8 distinct tiles cycled with distinct Philox streams), 32 requests; "
                           "saturated (all submitted at once) and Poisson arrivals at 0.7x the saturated rate; "
-                          "HBM budget 120 GB, 10 iterations per round; 512 samples, 100 iterations"),
+                          "HBM budget 120 GB, at most 262,144 resident contours, 10 iterations per round; 512 "
+                          "samples, 100 iterations"),
 }
 
 
@@ -619,9 +620,9 @@ def serve_arm(args, wl, rank, world, dev):
         return int(np.prod([max(1, int(math.floor(n * sp / wl["stride"]))) for n, sp in
                             zip(t.shape_xyz, t.spacing)]))
 
-    def run(arrivals):
+    def run(arrivals, cap=wl["contour_cap"]):
         srv = ac.Server(params, ac.AC_U16, 3, wl["stride"], E0, hbm_budget_bytes=int(wl["budget_gb"] * 1e9),
-                        iters_per_round=wl["ipr"])
+                        iters_per_round=wl["ipr"], max_resident_contours=cap)
         t0 = time.perf_counter()
         tickets = []
         for i, a in enumerate(arrivals):
@@ -654,6 +655,9 @@ def serve_arm(args, wl, rank, world, dev):
     arrivals = [a - arrivals[0] for a in arrivals]
     wall_p, samples_p, voxels_p, res_p, st_p = run(arrivals)
     clk = clocks.stop()
+    # the same saturated stream without the contour cap: every tile resident at once
+    wall_u, samples_u, _, res_u, _ = run([0.0] * n_req, cap=0)
+    lat_u = np.array([r["total_ms"] for r in res_u])
     reducer = torch_max_reducer(dev) if dist_on else None
     t_ms, value = aggregate_ranks([wall * 1e3], samples, world, reducer)
     lat = np.array([r["total_ms"] for r in res_p])
@@ -683,7 +687,10 @@ def serve_arm(args, wl, rank, world, dev):
                         "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
                         "queue_ms_p50": float(np.median([r["queue_ms"] for r in res_p])),
                         "rounds_saturated": st_sat["rounds"], "rounds_poisson": st_p["rounds"],
-                        "peak_resident_gb": st_sat["peak_resident_bytes"] / 1e9},
+                        "peak_resident_gb": st_sat["peak_resident_bytes"] / 1e9,
+                        "uncapped_saturated": {"samples_per_s": samples_u / wall_u,
+                                               "latency_ms_p50": float(np.percentile(lat_u, 50)),
+                                               "latency_ms_p99": float(np.percentile(lat_u, 99))}},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s",
                          "frac": achieved / peak, "traffic": None,

@@ -13,7 +13,9 @@
  * ac_batch_item).  Between rounds, waiting tiles are admitted in arrival order
  * while the estimated device bytes of the resident tiles stay within
  * `hbm_budget_bytes`, and tiles that finished are localized, their cells kept for
- * the caller, and their device memory released.  Because the Philox counter of a
+ * the caller, and their device memory released (a tile is admitted when it fits
+ * the byte budget, the tile cap and the contour cap; the first tile in line is
+ * always admitted when nothing is resident).  Because the Philox counter of a
  * sample is (j, n, k, stream_id) with one key for the server, a tile's cells and
  * energies do not depend on which tiles it shared rounds with: they equal those
  * of ac_evolve on that tile alone with the server's evolve parameters and the
@@ -45,6 +47,10 @@ typedef struct {
     int32_t iters_per_round;    /* iterations per tile per round (>= 1)            */
     int32_t max_resident;       /* tiles resident at once; 0: budget only          */
     int64_t hbm_budget_bytes;   /* admission budget for resident tiles (> 0)       */
+    int64_t max_resident_contours; /* contours resident at once (lattice sizes);
+                                   0: no limit.  A few times what the GPU holds in
+                                   flight keeps it busy while tiles finish in
+                                   arrival order instead of together             */
 } ac_server_params;
 
 /* Per-tile outcome, filled by ac_server_wait. */

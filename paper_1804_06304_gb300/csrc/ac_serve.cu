@@ -38,7 +38,7 @@ struct Tile {
     float spacing[3] = {1, 1, 1};
     float scale = 1.0f;
     uint32_t stream_id = 0;
-    int64_t contours = 0, voxels = 0, est_bytes = 0;
+    int64_t contours = 0, voxels = 0, est_bytes = 0, lattice = 0;
     Clock::time_point t_submit, t_admit, t_done;
     ac_volume *vol = nullptr;
     ac_contours *ctr = nullptr;
@@ -76,6 +76,7 @@ struct ac_server {
     int64_t next_ticket = 1;
     bool stop = false;
     int64_t resident_bytes = 0, peak_bytes = 0, rounds = 0, completed = 0, failed = 0, finished = 0;
+    int64_t resident_contours = 0;         // lattice sizes of the resident tiles
     ac_plan *plan = nullptr;               // worker only
 };
 
@@ -124,8 +125,12 @@ void serve_loop(ac_server *S)
                 const int64_t n_res = (int64_t)(S->resident.size() + admit.size());
                 if (n_res > 0 && S->resident_bytes + t->est_bytes > S->p.hbm_budget_bytes) break;
                 if (S->p.max_resident > 0 && n_res >= S->p.max_resident) break;
+                if (n_res > 0 && S->p.max_resident_contours > 0 &&
+                    S->resident_contours + t->lattice > S->p.max_resident_contours)
+                    break;
                 S->pending.pop_front();
                 S->resident_bytes += t->est_bytes;
+                S->resident_contours += t->lattice;
                 S->peak_bytes = std::max(S->peak_bytes, S->resident_bytes);
                 admit.push_back(t);
             }
@@ -147,6 +152,7 @@ void serve_loop(ac_server *S)
             if (s != AC_OK) {
                 release_device(t);
                 S->resident_bytes -= t->est_bytes;
+                S->resident_contours -= t->lattice;
                 finish_locked(S, t, s, err);
                 S->cv_done.notify_all();
             } else {
@@ -184,6 +190,7 @@ void serve_loop(ac_server *S)
             for (Tile *t : S->resident) {
                 release_device(t);
                 S->resident_bytes -= t->est_bytes;
+                S->resident_contours -= t->lattice;
                 finish_locked(S, t, s, err);
             }
             S->resident.clear();
@@ -226,6 +233,7 @@ void serve_loop(ac_server *S)
         S->resident = keep;
         for (size_t i = 0; i < done.size(); ++i) {
             S->resident_bytes -= done[i]->est_bytes;
+            S->resident_contours -= done[i]->lattice;
             finish_locked(S, done[i], outcome[i].first, outcome[i].second);
         }
         S->cv_done.notify_all();
@@ -248,6 +256,7 @@ extern "C" ac_status ac_server_create(const ac_server_params *params, ac_server 
     if (p.iters_per_round < 1) AC_FAIL(AC_ERR_ARG, "ac_server_create: iters_per_round must be >= 1");
     if (p.max_resident < 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: max_resident must be >= 0");
     if (p.hbm_budget_bytes <= 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: hbm_budget_bytes must be positive");
+    if (p.max_resident_contours < 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: max_resident_contours must be >= 0");
     ac_status s = ac::check_evolve_params(&p.evolve);
     if (s != AC_OK) return s;
     ac_server *S = new ac_server();
@@ -292,6 +301,7 @@ extern "C" ac_status ac_server_submit(ac_server *S, const void *data_host, const
     const int es = elem_bytes(S->p.dtype);
     const int64_t pitch = (dims[0] * es + 15) / 16 * 16;
     const int64_t C = lattice_contours(t->dims, t->spacing, nd, S->p.stride);
+    t->lattice = C;
     t->est_bytes = pitch * dims[1] * dims[2] + 100 * C + (1 << 20);
     if (t->est_bytes > S->p.hbm_budget_bytes) {
         delete t;

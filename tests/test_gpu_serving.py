@@ -78,14 +78,21 @@ def test_alone_equals_mix(ac, tiles):
     srv.close()
 
 
-@pytest.mark.parametrize("mode", ["budget", "one_at_a_time"])
+def _lattice(volume):
+    nz, ny, nx = volume.shape
+    return max(1, int(nx // STRIDE)) * max(1, int(ny // STRIDE)) * max(1, int(nz // STRIDE))
+
+
+@pytest.mark.parametrize("mode", ["budget", "one_at_a_time", "contours"])
 def test_admission_limits(ac, tiles, mode):
     p = _params(ac)
     want = [_alone(ac, t.volume, t.spacing, p, 7 + i) for i, t in enumerate(tiles)]
     est = [_est_bytes(t.volume, 2) for t in tiles]
     budget = int(1.2 * max(est)) if mode == "budget" else 120 << 30
+    cap = max(_lattice(t.volume) for t in tiles) if mode == "contours" else 0
     srv = ac.Server(p, ac.AC_U16, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=budget,
-                    iters_per_round=5, max_resident=1 if mode == "one_at_a_time" else 0)
+                    iters_per_round=5, max_resident=1 if mode == "one_at_a_time" else 0,
+                    max_resident_contours=cap)
     tickets = [srv.submit(t.volume, t.spacing, stream_id=7 + i) for i, t in enumerate(tiles)]
     for tk, w, e in zip(tickets, want, est):
         cells, res = srv.wait(tk, timeout=300)
@@ -96,6 +103,8 @@ def test_admission_limits(ac, tiles, mode):
     if mode == "one_at_a_time":
         assert st["peak_resident_bytes"] == max(est)
         assert st["rounds"] == len(tiles) * math.ceil(T / 5)
+    elif mode == "contours":
+        assert st["rounds"] > math.ceil(T / 5) and st["peak_resident_bytes"] < sum(est)
     else:
         assert st["peak_resident_bytes"] < sum(est)       # the budget held tiles back
         big = np.zeros((budget // (2 * 64 * 64) + 8, 64, 64), np.uint16)
