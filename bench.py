@@ -490,7 +490,11 @@ def batch_arm(args, wl, rank, world, dev):
     R0 = wl["stride"] / math.sqrt(1.5)
     params = ac.default_params(3, R0, 170.0, N=wl["N"], T=wl["T"], seed=1000 + rank, compensated=args.compensated)
     t0 = time.perf_counter()
-    params = ac.ac_autotune(C, params)
+    fixed = tuple(int(x) for x in args.brick.split(","))
+    if args.lanes or args.warps or any(fixed):   # an explicit configuration skips the autotuner
+        params = dataclasses.replace(params, lanes_per_contour=args.lanes, warps_per_block=args.warps, brick=fixed)
+    else:
+        params = ac.ac_autotune(C, params)
     tune_s = time.perf_counter() - t0
     items = [(i, 1, wl["T"], 0) for i in range(len(C))]
     plan = ac.ac_plan_create(C, params, items=items)

@@ -242,7 +242,7 @@ void ac_destroy_plan(ac_plan *plan);
 
 /*
  * ac_autotune -- choose lanes_per_contour, brick and warps_per_block for these sets
- * by timing short trial launches (3 iterations) of candidate configurations on
+ * by timing short trial launches (up to 8 iterations, best of two) of candidate configurations on
  * copies of their state (the sets are not modified), and write them into
  * *params.  A fixed lanes_per_contour is kept; the plain path is left untouched.
  * Results are cached per workload shape (dimension, voxel type, N, summation and

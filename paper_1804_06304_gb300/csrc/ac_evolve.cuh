@@ -376,8 +376,17 @@ __device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DI
                                                uint32_t n, uint32_t k, uint32_t stream, int lig, KSum *acc)
 {
     if constexpr (DIM == 3) {
-        // samples j and j + G of this lane form a pair
-        for (int j = lig; j < a.N; j += 2 * G) {
+        // samples j, j + G, j + 2G, j + 3G of this lane are computed together (more
+        // independent work per warp) and summed in two roundings before one
+        // compensated addition; the rest go in pairs
+        int j = lig;
+        for (; j + 3 * G < a.N; j += 4 * G) {
+            add_terms4<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, (uint32_t)j, n, k, stream),
+                                  sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + G), n, k, stream),
+                                  sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + 2 * G), n, k, stream),
+                                  sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + 3 * G), n, k, stream));
+        }
+        for (; j < a.N; j += 2 * G) {
             const Terms x = sample3<DIM, ACC>(gat, ic, a, (uint32_t)j, n, k, stream);
             if (j + G < a.N) add_terms<DIM, COMP>(acc, x, sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + G), n, k, stream));
             else add_terms<DIM, COMP>(acc, x);
