@@ -337,8 +337,10 @@ def default_params(ndim: int, R0: float, contrast: float, N: int, T: int, seed: 
 
 
 def default_E0(ndim: int, contrast: float) -> float:
-    """Half the ideal-blob minimum energy (-A pi/12 in 3D, -A pi/8 in 2D)."""
-    return -math.pi * contrast / 24.0 if ndim == 3 else -math.pi * contrast / 16.0
+    """A quarter of the ideal-blob minimum energy (-A pi/12 in 3D, -A pi/8 in 2D):
+    real nuclei (blurred, elongated, dimmer than the typical contrast A) reach
+    only part of the ideal minimum."""
+    return -math.pi * contrast / 48.0 if ndim == 3 else -math.pi * contrast / 32.0
 
 
 def ac_evolve(ctr: Contours, params: EvolveParams, trace=None, stream=None):
