@@ -156,29 +156,29 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------ oracle leg
-def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0):
-    """Time the FP64 oracle (all host cores) on a random subset of the workload's
-    contours, sized to take about `seconds`; returns (samples/s, threads, sample text)."""
+def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0, threads: int = 0):
+    """Time the FP64 oracle (all host cores, or `threads`) on a random subset of the
+    workload's contours, sized to take about `seconds`; returns (samples/s, threads,
+    sample text)."""
     from oracle import oracle
-    from paper_1804_06304_gb300 import ac as _ac_defaults  # noqa: F401  (defaults only)
     ndim = wl["ndim"]
     seeds = oracle.seed_lattice(ndim, s.shape_xyz, spacing, wl["stride"])
     R0 = seeds[0, 3]
     op = oracle.make_params(ndim, wl["N"], wl["T"], eps0=8 * R0 * R0 / s.contrast, dR=1.0,
                             Rmin=max(0.5, 0.5 * R0), Rmax=3 * R0, max_step=0.5, seed=7)
     img = oracle.VolumeImage(vol, spacing)
-    threads = oracle.max_threads()
+    threads = threads or oracle.max_threads()
     rng = np.random.default_rng(rng_seed)
     pilot = min(len(seeds), max(threads * 2, 16))
     idx = rng.choice(len(seeds), pilot, replace=False)
     t0 = time.perf_counter()
-    oracle.evolve(img, op, seeds[idx], ids=idx)
+    oracle.evolve(img, op, seeds[idx], ids=idx, nthreads=threads)
     dt = time.perf_counter() - t0
     per = dt / pilot
     m = int(min(len(seeds), max(pilot, seconds / max(per, 1e-9))))
     idx = rng.choice(len(seeds), m, replace=False)
     t0 = time.perf_counter()
-    oracle.evolve(img, op, seeds[idx], ids=idx)
+    oracle.evolve(img, op, seeds[idx], ids=idx, nthreads=threads)
     dt = time.perf_counter() - t0
     samples = m * wl["N"] * wl["T"]
     return samples / dt, threads, f"{m} of {len(seeds)} contours (random, seed {rng_seed}), all {wl['T']} iterations"
@@ -423,7 +423,9 @@ def main(argv=None):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.path != "grid":
         v, thr, desc = oracle_sample(s, vol, wl, spacing, args.cpu_seconds)
-        cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc}
+        v1, _, desc1 = oracle_sample(s, vol, wl, spacing, min(3.0, args.cpu_seconds), rng_seed=1, threads=1)
+        cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc,
+               "one_thread": {"value": v1, "sample": desc1}}
     citers = C.count * wl["T"]
 
     if rank == 0 and args.path == "grid":
@@ -448,6 +450,8 @@ def main(argv=None):
             "metric": "MC contour samples/s (whole path: ingest, seed, evolve, localize)",
             "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "step_ms": {"median": float(np.median(step_ms)), "p99": float(np.percentile(step_ms, 99)),
+                        "min": float(np.min(step_ms)), "max": float(np.max(step_ms))},
             "dtype": "f32 arithmetic on " + str(vol.dtype) + " voxels", "data": "synthetic",
             "config": {"workload": args.workload + (f"@{args.size}" if args.size else ""), "desc": wl["desc"],
                        "contours": C.count, "samples": wl["N"],

@@ -521,8 +521,8 @@ void or_evolve(const or_image *img, const or_params *P, int64_t C, const int64_t
                double *cR, double *E_out, double *trace, int32_t *stops, int32_t *n_eval, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4)
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
 #endif
     for (int64_t i = 0; i < C; ++i) {
         double p[3] = {cR[4 * i] - cR[4 * i + 3], cR[4 * i + 1], cR[4 * i + 2]};
@@ -698,8 +698,8 @@ void or_eval_many(const or_image *img, const or_params *P, int64_t m, const doub
                   const int64_t *ks, double *res, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
 #endif
     for (int64_t i = 0; i < m; ++i)
         or_eval_cr(img, P, cR + 4 * i, cR[4 * i + 3], iters[i], ks[i], res + (int64_t)OR_RES_LEN * i);
