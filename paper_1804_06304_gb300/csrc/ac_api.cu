@@ -424,8 +424,8 @@ ac_status check_params(const ac_evolve_params *p)
     if (p->path != AC_PATH_BRICK && p->path != AC_PATH_PLAIN && p->path != AC_PATH_GRID)
         AC_FAIL(AC_ERR_ARG, "ac_evolve: unknown path");
     if (p->path == AC_PATH_GRID && p->lanes_per_contour != 0 && p->lanes_per_contour != 8 &&
-        p->lanes_per_contour != 16)
-        AC_FAIL(AC_ERR_ARG, "ac_evolve: the grid path takes 8 or 16 lanes per contour");
+        p->lanes_per_contour != 16 && p->lanes_per_contour != 4)
+        AC_FAIL(AC_ERR_ARG, "ac_evolve: the grid path takes 4 (2D, compensated), 8 or 16 lanes per contour");
     if (!(p->freeze_tol >= 0.0f) || !std::isfinite(p->freeze_tol)) AC_FAIL(AC_ERR_ARG, "ac_evolve: freeze_tol must be >= 0");
     if (p->freeze_iters < 0 || p->freeze_iters > 0xFFFF) AC_FAIL(AC_ERR_ARG, "ac_evolve: freeze_iters in [0, 65535]");
     if (p->cull_iter < 0) AC_FAIL(AC_ERR_ARG, "ac_evolve: cull_iter must be >= 0");
@@ -460,7 +460,10 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     pl.comp = p->compensated != 0;
     if (pl.grid) {   // no samples: no sampling mode; lanes walk the chords of the ball
         pl.acc = false;
-        pl.G = p->lanes_per_contour ? p->lanes_per_contour : 8;
+        // measured best: 4 lanes in 2D (compensated sums), 8 in 3D
+        pl.G = p->lanes_per_contour ? p->lanes_per_contour : (vol->ndim == 2 && pl.comp ? 4 : 8);
+        if (pl.G == 4 && (vol->ndim != 2 || !pl.comp))
+            AC_FAIL(AC_ERR_ARG, "ac_evolve: 4 lanes on the grid path are built for 2D with compensated sums");
         pl.warps = p->warps_per_block ? p->warps_per_block : 8;
         pl.quad_off = 0;
         return AC_OK;

@@ -44,9 +44,11 @@ __device__ __forceinline__ Step eval_grid(const VolDesc &V, const EvolveArgs &a,
             const int i1 = (int)floorf((c[0] + chord) * V.inv_sp[0]);
             const int yy = min(max(jy, 0), V.n[1] - 1);
             const int64_t row = (int64_t)zz * V.pitch_z + (int64_t)yy * V.pitch_y;
-            for (int ix = i0 + lig; ix <= i1; ix += G) {
+            // the terms of voxel ix of this row
+            auto terms = [&](int ix, float *v) {
                 const float dx = fmaf((float)ix, V.sp[0], -c[0]);
-                const float I = ldg_f<T>(data + checked(row + min(max(ix, 0), V.n[0] - 1), nvox, V.status));
+                const float I = ix <= i1 ? ldg_f<T>(data + checked(row + min(max(ix, 0), V.n[0] - 1), nvox, V.status))
+                                         : 0.0f;
                 const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 const float t1 = fmaf(r, a.inv_dr, B1), t2 = fmaf(r, a.inv_dR, B2);
                 const float r1 = __saturatef(t1), r2 = __saturatef(t2);
@@ -55,7 +57,31 @@ __device__ __forceinline__ Step eval_grid(const VolDesc &V, const EvolveArgs &a,
                 const float dSdR = (b1 ? a.kR1 : 0.0f) + (b2 ? a.kR2 : 0.0f);
                 // -S'(r) I / r: the direction (x - c) / r without a division by zero at the centre
                 const float g = r > 0.0f ? ((b1 ? a.kr1 : 0.0f) + (b2 ? a.kr2 : 0.0f)) * I / r : 0.0f;
-                const float v[5] = {S * I, dSdR * I, g * dx, g * dy, g * dz};
+                v[0] = S * I;
+                v[1] = dSdR * I;
+                v[2] = g * dx;
+                v[3] = g * dy;
+                v[4] = g * dz;
+            };
+            // two voxels per step (ix and ix + G), summed in one rounding before the
+            // compensated addition: two independent chains of work per lane.  In 2D
+            // every step takes a pair (a voxel beyond the chord adds zero: cheaper than
+            // a divergent tail on these latency-bound rows); in 3D, whose rows are
+            // shorter, pairs only while both voxels lie on the chord, then a single one
+            int ix = i0 + lig;
+            for (; DIM == 2 ? ix <= i1 : ix + G <= i1; ix += 2 * G) {
+                float v[5], w[5];
+                terms(ix, v);
+                terms(ix + G, w);
+#pragma unroll
+                for (int m = 0; m < (DIM == 3 ? 5 : 4); ++m) {
+                    if (COMP) kadd(acc[m], v[m] + w[m]);
+                    else acc[m].s += v[m] + w[m];
+                }
+            }
+            if (ix <= i1) {
+                float v[5];
+                terms(ix, v);
 #pragma unroll
                 for (int m = 0; m < (DIM == 3 ? 5 : 4); ++m) {
                     if (COMP) kadd(acc[m], v[m]);
@@ -84,7 +110,7 @@ __device__ __forceinline__ Step eval_grid(const VolDesc &V, const EvolveArgs &a,
 }
 
 template <int DIM, typename T, int G, bool COMP>
-__global__ void __maxnreg__(128) evolve_grid_kernel(const __grid_constant__ EvolveArgs a)
+__global__ void __maxnreg__(80) evolve_grid_kernel(const __grid_constant__ EvolveArgs a)
 {
     unsigned int evals = 0;
     const int lig = threadIdx.x % G;
@@ -145,14 +171,14 @@ cudaError_t launch_grid_t(const EvolveArgs &a, int warps, int64_t grid, cudaStre
     return cudaGetLastError();
 }
 
-// 8 and 16 lanes, compensated and plain sums, 2D and 3D.
+// 8 and 16 lanes, compensated and plain sums, 2D and 3D; 4 lanes in 2D (compensated).
 template <typename T>
 cudaError_t launch_grid_dtype(const EvolveArgs &a, int G, bool comp, int warps, int64_t grid, cudaStream_t st)
 {
 #define AC_GRID(DIM, GG, CC) \
     if (a.ndim == DIM && G == GG && comp == CC) return launch_grid_t<DIM, T, GG, CC>(a, warps, grid, st);
     AC_GRID(3, 8, true) AC_GRID(3, 16, true) AC_GRID(3, 8, false) AC_GRID(3, 16, false)
-    AC_GRID(2, 8, true) AC_GRID(2, 16, true) AC_GRID(2, 8, false) AC_GRID(2, 16, false)
+    AC_GRID(2, 8, true) AC_GRID(2, 16, true) AC_GRID(2, 8, false) AC_GRID(2, 16, false) AC_GRID(2, 4, true)
 #undef AC_GRID
     return cudaErrorInvalidValue;
 }

@@ -71,10 +71,12 @@ def test_grid_teacher_forced_anisotropic_u16_f16(ac, oracle, aniso3d):
         assert frac >= 0.9999, (vol.dtype, frac, nflag, worst, bad)
 
 
-def test_grid_teacher_forced_2d(ac, oracle, crop2d):
+@pytest.mark.parametrize("G,comp", [(0, 1), (8, 1), (16, 0)])
+def test_grid_teacher_forced_2d(ac, oracle, crop2d, G, comp):
     s = crop2d
     R0 = 6.0 / math.sqrt(1.5)
-    p = ac.default_params(2, R0, s.contrast, N=1, T=20, seed=8, path=ac.AC_PATH_GRID)
+    p = ac.default_params(2, R0, s.contrast, N=1, T=20, seed=8, path=ac.AC_PATH_GRID, lanes_per_contour=G,
+                          compensated=comp)
     r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(0, 1764))
     img = P.oracle_image(oracle, s.volume, s.spacing)
     frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 0, 1)
