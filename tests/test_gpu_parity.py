@@ -372,6 +372,26 @@ def test_invalid_parameters_rejected(ac, small3d):
 
 
 # ------------------------------------------------------------------ full size, sampled
+def test_full_size_3d_sampled_parity(ac, oracle):
+    """The 1024x1024x256 uint16 brain-like workload (spacing 1:1:2) in the
+    benchmark's launch configuration (N = 512, T = 100, automatic brick plan); the
+    oracle re-evaluates a stripe of 256 contours in the middle of the volume at
+    every iteration."""
+    from paper_1804_06304_gb300 import synth
+    s = synth.brain_3d(2, with_f16=False)
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(3, R0, s.contrast, N=512, T=100, seed=1000)
+    k0 = 170 * 170 * 42 + 170 * 85     # a row through the middle plane
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(k0, k0 + 256))
+    assert r["final"].shape[1] == 170 * 170 * 85
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], k0, 1)
+    assert frac >= 0.9999, (frac, worst, bad)
+    assert np.all(np.isfinite(r["final"]))
+    fast, clamped, glob = ac.ac_evolve_stats(r["ctr"])
+    assert fast > 0.9 * (fast + clamped + glob)
+
+
 def test_full_size_2d_sampled_parity(ac, oracle):
     """The 4096^2 workload in the benchmark's launch configuration; the oracle
     re-evaluates a sampled stripe of contours at every iteration."""
