@@ -250,6 +250,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 reference measurement")
+    ap.add_argument("--count", type=int, default=0, help="batch-3d: number of volumes (profiling captures)")
     args = ap.parse_args(argv)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -484,7 +485,7 @@ def batch_arm(args, wl, rank, world, dev):
     from paper_1804_06304_gb300 import ac, synth
 
     dist_on = world > 1
-    vols = synth.batch_3d(wl["seed"] + rank, count=wl["count"])
+    vols = synth.batch_3d(wl["seed"] + rank, count=args.count or wl["count"])
     V, C = [], []
     pinned = []
     for sv in vols:
