@@ -95,9 +95,10 @@ ac_status ac_load_volume(ac_volume *vol, const void *data, int data_on_device, i
  * leftover split evenly between both ends of each axis; contour index k runs x
  * fastest.  Explicit: `explicit_cR` (host, n_explicit rows of cx, cy, cz, R as
  * float32) places contour k at row k; centres are clamped into the box of voxel
- * centres and radii must lie in (0, 1e6].  The contour index k enters the Philox
- * counter, so results do not depend on how contours are scheduled.
- * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ * centres and radii must lie in (0, 1e6]; a non-NULL `explicit_cR` with
+ * n_explicit = 0 gives an empty set (evolution and localization do nothing on it).
+ * The contour index k enters the Philox counter, so results do not depend on how
+ * contours are scheduled.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
  */
 typedef struct {
     double stride;   /* lattice stride, physical units; ignored when n_explicit > 0 */

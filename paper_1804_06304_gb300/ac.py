@@ -274,7 +274,8 @@ def ac_seed(vol: Volume, stride: float | None = None, R0: float = 0.0, explicit=
     out = ct.c_void_p()
     if explicit is not None:
         e = np.ascontiguousarray(explicit, dtype=np.float32).reshape(-1, 4)
-        _check(l.ac_seed(vol.handle, ct.byref(p), ct.c_void_p(e.ctypes.data), len(e), ct.c_void_p(_stream(stream)),
+        buf = e if len(e) else np.zeros((1, 4), np.float32)   # a valid pointer for an empty set
+        _check(l.ac_seed(vol.handle, ct.byref(p), ct.c_void_p(buf.ctypes.data), len(e), ct.c_void_p(_stream(stream)),
                          ct.byref(out)))
     else:
         _check(l.ac_seed(vol.handle, ct.byref(p), None, 0, ct.c_void_p(_stream(stream)), ct.byref(out)))

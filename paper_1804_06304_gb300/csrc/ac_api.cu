@@ -205,6 +205,14 @@ extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const
     *out = nullptr;
     if (!vol) AC_FAIL(AC_ERR_ARG, "ac_seed: vol is NULL");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (n_explicit < 0) AC_FAIL(AC_ERR_ARG, "ac_seed: n_explicit is negative");
+    if (explicit_cR && n_explicit == 0) {   // an empty set
+        ac_contours *c = nullptr;
+        ac_status s = make_contours(vol, 0, &c);
+        if (s != AC_OK) return s;
+        *out = c;
+        return AC_OK;
+    }
     if (n_explicit > 0) {
         if (!explicit_cR) AC_FAIL(AC_ERR_ARG, "ac_seed: explicit_cR is NULL");
         if (n_explicit >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_seed: too many contours");
@@ -697,7 +705,7 @@ ac_status apply_items(Prepared &pr, const ac_batch_item *items, const ac_evolve_
         a.first_iter = lo;
         a.last_iter = hi;
     }
-    for (int i = 0; i < pr.n_sets; ++i) {
+    for (int i = 0; i < pr.n_sets && i < (int)pr.desc.size(); ++i) {   // no descriptors: only empty sets
         VolDesc &d = pr.desc[i];
         d.stream = items ? items[i].stream_id : p->stream_id;
         d.first_iter = items ? items[i].first_iter : a.first_iter;
@@ -726,6 +734,12 @@ ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int
         total += sets[i]->C;
     }
     if (total >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_evolve: too many contours in one launch");
+    if (total == 0) {   // only empty sets: nothing to plan or launch
+        pr = Prepared();
+        pr.n_sets = n_sets;
+        pr.owner = sets[0];
+        return AC_OK;
+    }
     Plan &pl = pr.pl;
     s = plan_evolve(v0, stride_hint, r_hint, p, pl);
     if (s != AC_OK) return s;
@@ -1306,6 +1320,7 @@ extern "C" ac_status ac_plan_launch(ac_plan *pl, int use_graph, void *cuda_strea
     g_err.clear();
     if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_launch: NULL plan");
     if (!pl->valid) AC_FAIL(AC_ERR_STATE, "ac_plan_launch: the plan has no sets (a rebind failed)");
+    if (pl->pr.total == 0) return AC_OK;   // only empty sets
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!use_graph) return enqueue_prepared(pl->pr, pl->sc, st, nullptr);
     if (!pl->exec) {
@@ -1372,11 +1387,14 @@ extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_ev
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const ac_volume *v0 = sets[0]->vol;
     double stride_hint = 0, r_hint = 0;
+    int64_t total = 0;
     for (int i = 0; i < n_sets; ++i) {
         if (!sets[i] || !sets[i]->vol) AC_FAIL(AC_ERR_ARG, "ac_autotune: NULL contour set");
         stride_hint = std::max(stride_hint, sets[i]->stride_hint);
         r_hint = std::max(r_hint, sets[i]->r_hint);
+        total += sets[i]->C;
     }
+    if (total == 0) return AC_OK;   // only empty sets: nothing to time
     const bool comp = params->compensated != 0;
     const bool acc = params->sampling == 1 || (params->sampling == 0 && params->N < 64);
     const TuneKey key{v0->ndim, (int)v0->dtype, params->N, params->lanes_per_contour, comp, acc,

@@ -4,6 +4,7 @@ Per-iteration (teacher-forced) energies and gradients within 1e-5 of the oracle'
 magnitude-scaled value, final centres within 0.25 voxel, detection-set agreement
 >= 0.999, identical Philox words and identical localization on identical inputs.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -405,3 +406,33 @@ def test_full_size_2d_sampled_parity(ac, oracle):
     frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 200_000, 1)
     assert frac >= 0.9999, (frac, worst, bad)
     assert np.all(np.isfinite(r["final"]))
+
+
+def test_empty_set_and_single_iteration(ac, small3d):
+    """Degenerate inputs: an explicitly empty contour set evolves, batches, plans
+    and localizes to nothing; T = 1 is one evaluation and no update."""
+    s = small3d
+    V = ac.ac_create_volume(s.volume, s.spacing)
+    E = ac.ac_seed(V, explicit=np.zeros((0, 4), np.float32))
+    assert E.count == 0
+    p = _p3(ac, s, T=5)
+    ac.ac_evolve(E, p)
+    assert ac.ac_get_state(E).shape == (5, 0)
+    assert len(ac.ac_localize(E, ac.default_E0(3, s.contrast))) == 0
+    assert ac.ac_evolve_stops(E) == (0, 0)
+    assert ac.ac_autotune([E], p) == p
+    full = ac.ac_seed(V, stride=4.0)
+    ref = ac.ac_seed(V, stride=4.0)
+    ac.ac_evolve_batch([E, full], p, items=[(1, 1, 5, 0), (2, 1, 5, 0)])   # an empty set in a batch
+    ac.ac_evolve(ref, dataclasses.replace(p, stream_id=2))
+    np.testing.assert_array_equal(ac.ac_get_state(full), ac.ac_get_state(ref))
+    plan = ac.ac_plan_create([E], p)
+    ac.ac_plan_set_items(plan, [(0, 1, 3, 0)])
+    ac.ac_plan_launch(plan, use_graph=True)
+    # T = 1: the energy of the seed state is evaluated, the state is not moved
+    one = ac.ac_seed(V, stride=4.0)
+    init = ac.ac_get_state(one)
+    ac.ac_evolve(one, _p3(ac, s, T=1))
+    after = ac.ac_get_state(one)
+    np.testing.assert_array_equal(after[:4], init[:4])
+    assert np.any(after[4] != 0)
