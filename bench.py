@@ -74,8 +74,8 @@ WORKLOADS = {
                      desc="request loop over uint16 tiles 128^3..1024x1024x64 (log-uniform voxel count, brain-3d "
                           "nucleus model, 8 distinct tiles cycled with distinct Philox streams), 32 requests; "
                           "saturated (all submitted at once) and Poisson arrivals at 0.7x the saturated rate; "
-                          "HBM budget 120 GB, at most 262,144 resident contours, 10 iterations per round; 512 "
-                          "samples, 100 iterations"),
+                          "HBM budget 120 GB, at most 262,144 resident contours, 10 iterations per round (up "
+                          "to 8x for small tiles); 512 samples, 100 iterations"),
 }
 
 
@@ -629,9 +629,9 @@ def serve_arm(args, wl, rank, world, dev):
         return int(np.prod([max(1, int(math.floor(n * sp / wl["stride"]))) for n, sp in
                             zip(t.shape_xyz, t.spacing)]))
 
-    def run(arrivals, cap=wl["contour_cap"]):
+    def run(arrivals, cap=wl["contour_cap"], balance=True):
         srv = ac.Server(params, ac.AC_U16, 3, wl["stride"], E0, hbm_budget_bytes=int(wl["budget_gb"] * 1e9),
-                        iters_per_round=wl["ipr"], max_resident_contours=cap)
+                        iters_per_round=wl["ipr"], max_resident_contours=cap, balance_rounds=balance)
         t0 = time.perf_counter()
         tickets = []
         for i, a in enumerate(arrivals):
@@ -667,6 +667,9 @@ def serve_arm(args, wl, rank, world, dev):
     # the same saturated stream without the contour cap: every tile resident at once
     wall_u, samples_u, _, res_u, _ = run([0.0] * n_req, cap=0)
     lat_u = np.array([r["total_ms"] for r in res_u])
+    # the same Poisson stream with every tile advancing iters_per_round per round
+    _, _, _, res_nb, _ = run(arrivals, balance=False)
+    lat_nb = np.array([r["total_ms"] for r in res_nb])
     reducer = torch_max_reducer(dev) if dist_on else None
     t_ms, value = aggregate_ranks([wall * 1e3], samples, world, reducer)
     lat = np.array([r["total_ms"] for r in res_p])
@@ -697,6 +700,8 @@ def serve_arm(args, wl, rank, world, dev):
                         "queue_ms_p50": float(np.median([r["queue_ms"] for r in res_p])),
                         "rounds_saturated": st_sat["rounds"], "rounds_poisson": st_p["rounds"],
                         "peak_resident_gb": st_sat["peak_resident_bytes"] / 1e9,
+                        "poisson_unbalanced_rounds": {"latency_ms_p50": float(np.percentile(lat_nb, 50)),
+                                                      "latency_ms_p99": float(np.percentile(lat_nb, 99))},
                         "uncapped_saturated": {"samples_per_s": samples_u / wall_u,
                                                "latency_ms_p50": float(np.percentile(lat_u, 50)),
                                                "latency_ms_p99": float(np.percentile(lat_u, 99))}},

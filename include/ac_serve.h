@@ -51,6 +51,11 @@ typedef struct {
                                    0: no limit.  A few times what the GPU holds in
                                    flight keeps it busy while tiles finish in
                                    arrival order instead of together             */
+    int32_t balance_rounds;     /* 1: a tile advances iters_per_round x
+                                   min(8, largest resident lattice / its lattice)
+                                   iterations per round, so small tiles finish in
+                                   fewer rounds; 0: iters_per_round for every tile */
+    int32_t reserved_;          /* 0 */
 } ac_server_params;
 
 /* Per-tile outcome, filled by ac_server_wait. */

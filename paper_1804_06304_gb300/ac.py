@@ -70,7 +70,7 @@ class ac_server_params(ct.Structure):
     _fields_ = [("evolve", ac_evolve_params), ("dtype", ct.c_int32), ("ndim", ct.c_int32), ("stride", ct.c_float),
                 ("R0", ct.c_float), ("E0", ct.c_float), ("iters_per_round", ct.c_int32),
                 ("max_resident", ct.c_int32), ("hbm_budget_bytes", ct.c_int64),
-                ("max_resident_contours", ct.c_int64)]
+                ("max_resident_contours", ct.c_int64), ("balance_rounds", ct.c_int32), ("reserved_", ct.c_int32)]
 
 
 class ac_tile_result(ct.Structure):
@@ -525,13 +525,14 @@ class Server:
 
     def __init__(self, params: EvolveParams, dtype: int, ndim: int, stride: float, E0: float,
                  hbm_budget_bytes: int, iters_per_round: int = 10, max_resident: int = 0, R0: float = 0.0,
-                 max_resident_contours: int = 0):
+                 max_resident_contours: int = 0, balance_rounds: bool = True):
         sp = ac_server_params()
         sp.evolve = params.to_c()
         sp.dtype, sp.ndim, sp.stride, sp.R0, sp.E0 = int(dtype), int(ndim), float(stride), float(R0), float(E0)
         sp.iters_per_round, sp.max_resident, sp.hbm_budget_bytes = int(iters_per_round), int(max_resident), \
             int(hbm_budget_bytes)
         sp.max_resident_contours = int(max_resident_contours)
+        sp.balance_rounds = int(bool(balance_rounds))
         self.handle = None
         out = ct.c_void_p()
         _check(load().ac_server_create(ct.byref(sp), ct.byref(out)))

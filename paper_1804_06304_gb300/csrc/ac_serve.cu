@@ -167,9 +167,14 @@ void serve_loop(ac_server *S)
         const int n = (int)S->resident.size();
         std::vector<ac_contours *> sets(n);
         std::vector<ac_batch_item> items(n);
+        int64_t largest = 1;
+        for (Tile *t : S->resident) largest = std::max(largest, t->lattice);
         for (int i = 0; i < n; ++i) {
             Tile *t = S->resident[i];
-            const int m = std::min(S->p.iters_per_round, T - t->progress);
+            // a round lasts about as long as its largest tile's share: smaller tiles can
+            // take more iterations in it without lengthening it much
+            const int64_t f = S->p.balance_rounds ? std::min<int64_t>(8, std::max<int64_t>(1, largest / t->lattice)) : 1;
+            const int m = (int)std::min<int64_t>((int64_t)S->p.iters_per_round * f, T - t->progress);
             sets[i] = t->ctr;
             items[i].stream_id = t->stream_id;
             items[i].first_iter = t->progress + 1;
@@ -257,6 +262,7 @@ extern "C" ac_status ac_server_create(const ac_server_params *params, ac_server 
     if (p.max_resident < 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: max_resident must be >= 0");
     if (p.hbm_budget_bytes <= 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: hbm_budget_bytes must be positive");
     if (p.max_resident_contours < 0) AC_FAIL(AC_ERR_ARG, "ac_server_create: max_resident_contours must be >= 0");
+    if (p.balance_rounds != 0 && p.balance_rounds != 1) AC_FAIL(AC_ERR_ARG, "ac_server_create: balance_rounds must be 0 or 1");
     ac_status s = ac::check_evolve_params(&p.evolve);
     if (s != AC_OK) return s;
     ac_server *S = new ac_server();

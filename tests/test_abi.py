@@ -77,7 +77,7 @@ def test_struct_layouts_match_header(ac, tmp_path):
         "ac_localize_params": ["E0"],
         "ac_batch_item": ["stream_id", "first_iter", "n_iter", "update_last"],
         "ac_server_params": ["evolve", "dtype", "ndim", "stride", "R0", "E0", "iters_per_round", "max_resident",
-                             "hbm_budget_bytes", "max_resident_contours"],
+                             "hbm_budget_bytes", "max_resident_contours", "balance_rounds"],
         "ac_tile_result": ["ticket", "status", "rounds", "n_cells", "contours", "voxels", "est_bytes", "queue_ms",
                            "run_ms", "total_ms"],
         "ac_server_stats": ["pending", "resident", "finished", "completed", "failed", "rounds", "resident_bytes",
@@ -124,7 +124,7 @@ def test_server_argument_validation_without_device(ac):
     out = ct.c_void_p()
     for bad in [dict(dtype=7), dict(ndim=4), dict(stride=0.0), dict(R0=-1.0), dict(E0=float("nan")),
                 dict(iters_per_round=0), dict(max_resident=-1), dict(hbm_budget_bytes=0), dict(N=0),
-                dict(max_resident_contours=-5)]:
+                dict(max_resident_contours=-5), dict(balance_rounds=2)]:
         sp = params(**bad)
         assert l.ac_server_create(ct.byref(sp), ct.byref(out)) == ac.AC_ERR_ARG, bad
         assert not out.value

@@ -56,23 +56,34 @@ def _est_bytes(volume, elem):
     return pitch * ny * nz + 100 * C + (1 << 20)
 
 
-def test_alone_equals_mix(ac, tiles):
+@pytest.mark.parametrize("balance", [False, True])
+def test_alone_equals_mix(ac, tiles, balance):
     p = _params(ac)
-    want = [_alone(ac, t.volume, t.spacing, p, 100 + i) for i, t in enumerate(tiles)]
+    vols = [(t.volume, t.spacing) for t in tiles]
+    if balance:   # a small crop beside the large tiles, all submitted together
+        vols.append((np.ascontiguousarray(tiles[0].volume[:48, :48, :48]), tiles[0].spacing))
+    want = [_alone(ac, v, sp, p, 100 + i) for i, (v, sp) in enumerate(vols)]
     srv = ac.Server(p, ac.AC_U16, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=120 << 30,
-                    iters_per_round=7)
+                    iters_per_round=7, balance_rounds=balance)
     tickets = []
-    for i, t in enumerate(tiles):
-        tickets.append(srv.submit(t.volume, t.spacing, stream_id=100 + i))
-        time.sleep(0.003 * i)          # staggered arrivals: tiles join at different rounds
+    for i, (v, sp) in enumerate(vols):
+        tickets.append(srv.submit(v, sp, stream_id=100 + i))
+        if not balance:
+            time.sleep(0.003 * i)          # staggered arrivals: tiles join at different rounds
+    rounds = []
     for tk, w in zip(tickets, want):
         cells, res = srv.wait(tk, timeout=300)
-        assert res["status"] == 0 and res["rounds"] == math.ceil(T / 7)
+        assert res["status"] == 0 and res["rounds"] <= math.ceil(T / 7)
         assert res["total_ms"] >= res["run_ms"] > 0 and res["n_cells"] == len(cells)
+        rounds.append(res["rounds"])
         _same_cells(cells, w)
+    if balance:
+        assert rounds[-1] == 1                 # the crop: 8 x 7 iterations per round cover all 20
+    else:
+        assert rounds == [math.ceil(T / 7)] * len(vols)
     st = srv.stats()
-    assert st["completed"] == len(tiles) and st["resident"] == 0 and st["pending"] == 0 and st["finished"] == 0
-    assert st["rounds"] < len(tiles) * math.ceil(T / 7)   # rounds were shared
+    assert st["completed"] == len(vols) and st["resident"] == 0 and st["pending"] == 0 and st["finished"] == 0
+    assert st["rounds"] < len(vols) * math.ceil(T / 7)    # rounds were shared
     with pytest.raises(ac.ACError):
         srv.wait(tickets[0], timeout=0)                   # collected already
     srv.close()
@@ -92,7 +103,7 @@ def test_admission_limits(ac, tiles, mode):
     cap = max(_lattice(t.volume) for t in tiles) if mode == "contours" else 0
     srv = ac.Server(p, ac.AC_U16, 3, STRIDE, ac.default_E0(3, CONTRAST), hbm_budget_bytes=budget,
                     iters_per_round=5, max_resident=1 if mode == "one_at_a_time" else 0,
-                    max_resident_contours=cap)
+                    max_resident_contours=cap, balance_rounds=False)
     tickets = [srv.submit(t.volume, t.spacing, stream_id=7 + i) for i, t in enumerate(tiles)]
     for tk, w, e in zip(tickets, want, est):
         cells, res = srv.wait(tk, timeout=300)
