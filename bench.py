@@ -48,9 +48,10 @@ import numpy as np  # noqa: E402
 # per-iteration reduction and update are excluded.  Tabulated in the design notes.
 ALG_SLOTS_PER_SAMPLE = {2: 76.0, 3: 147.0}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
-# ncu capture of the current kernel (to be removed when the kernel changes): the
-# 2048^2 instance read 7.05 MB, scaled by 4 with the image area and contour count.
-DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.2e6}
+# ncu capture of the current kernel (to be removed when the kernel changes), scaled
+# with the volume and contour count: the 2048^2 instance of large-2d read 7.05 MB
+# (x 4), the 256x256x64 instance of brain-3d 9.51 MB (x 64).
+DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.2e6, ("brain-3d", "brick", 0, "native"): 608.3e6}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0
@@ -377,8 +378,8 @@ def main(argv=None):
     traffic = DRAM_BYTES_PER_LAUNCH.get((args.workload, args.path, args.size, args.dtype))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s", "frac": achieved / peak,
             "traffic": traffic,
-            "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: ncu capture of the "
-                            "2048^2 instance scaled x4 with the area", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
+            "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: ncu capture of a "
+                            "smaller instance (2048^2 / 256x256x64) scaled with the volume", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
             "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
 
