@@ -4,7 +4,6 @@ started."""
 import gc
 import math
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
