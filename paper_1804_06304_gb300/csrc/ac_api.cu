@@ -456,8 +456,8 @@ ac_status check_params(const ac_evolve_params *p)
 }
 
 // Brick interior, halo and staged-region size.  The halo covers a ball of 2.5x
-// the initial radius plus dR/2 and a margin (contours that outgrow it read from
-// global memory for that iteration).  A region starts at max(0, brick - halo)
+// (3D) or 3.5x (2D) the initial radius plus dR/2 and a margin (contours that
+// outgrow it read from global memory for that iteration).  A region starts at max(0, brick - halo)
 // (x rounded down to the 16-byte TMA alignment) and never extends past what the
 // volume needs; when the region would exceed the shared-memory budget the halo,
 // then the brick, shrinks.
@@ -478,8 +478,9 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     }
     pl.acc = p->sampling == 1 || (p->sampling == 0 && p->N < 64);
     if (pl.acc && !pl.comp) AC_FAIL(AC_ERR_ARG, "ac_evolve: accurate sampling is built with compensated sums only");
-    // lanes per contour: about 32 samples per lane (4 lanes only with compensated
-    // sums and fast sampling, otherwise at least 8), at most 32
+    // lanes per contour: 2D about 32 samples per lane (4 lanes only with compensated
+    // sums and fast sampling, otherwise at least 8); 3D about 8 to 16 (a warp per
+    // contour at N = 512); at most 32
     int G = p->lanes_per_contour;
     if (G == 0) {
         if (vol->ndim == 3) {   // 3D: a warp per contour unless N is small (measured best at N = 512)
