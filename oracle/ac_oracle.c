@@ -17,8 +17,13 @@
  *   update   p <- p - eps dE/dp, q <- q - eps dE/dq, eps = eps0/sqrt(n) (Eqs. 12-15)
  *   localize drop E > E0, overlap competition ||c'-c''|| < rho max(R',R'')
  *            with the lower energy surviving ("Results and Discussion")
+ *   grid     the same sums over the voxel centres inside R + dR/2, each weighted
+ *            by one voxel volume: Eq. 5 taken literally (the paper's integration
+ *            before it moved to sampling)
+ *   stopping optional rules for the paper's future work (convergence freeze, energy
+ *            culling): see or_params and or_evolve
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *   - the image between voxel centres is the trilinear (2D: bilinear) interpolant,
  *     clamp-to-edge outside the volume;
  *   - S(r;R) = -1 + 2 ramp((r - rho R)/dr) - ramp((r - R)/dR), ramp(t) =
