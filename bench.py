@@ -45,7 +45,7 @@ import numpy as np  # noqa: E402
 # accumulation of the four (2D) or five (3D) sums.  2D: 76 (a Philox block serves
 # two samples; one 128-bit load per bilinear gather); 3D: 147 (one block per
 # sample; eight 8/16-bit taps with exact integer-to-float conversion).  The
-# per-iteration reduction and update are excluded.  Tabulated in the design notes.
+# per-iteration reduction and update are excluded.
 ALG_SLOTS_PER_SAMPLE = {2: 76.0, 3: 147.0}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
 # ncu capture of the current kernel (to be removed when the kernel changes), scaled
