@@ -43,7 +43,7 @@ import numpy as np  # noqa: E402
 # sqrt / lg2+ex2 / sin / cos), index offsets, floor and fraction per axis, the
 # gather and multilinear interpolation, the two weight bands, and compensated
 # accumulation of the four (2D) or five (3D) sums.  2D: 76 (a Philox block serves
-# two samples; one 128-bit load per bilinear gather); 3D: 147 (one block per
+# two samples; one quad load per bilinear gather); 3D: 147 (one block per
 # sample; eight 8/16-bit taps with exact integer-to-float conversion).  The
 # per-iteration reduction and update are excluded.
 ALG_SLOTS_PER_SAMPLE = {2: 76.0, 3: 147.0}
