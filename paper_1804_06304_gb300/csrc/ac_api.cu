@@ -499,14 +499,36 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     // 3D regions are kept within half the shared memory so two CTAs share an SM
     const int64_t budget = vol->ndim == 3 ? 110 * 1024 : 200 * 1024;
     int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
+    // lattice cells per brick: 2x2x2 in 3D, 10x8 in 2D (measured best for 128
+    // samples: 80 contours of 4 lanes fill 10 warps, two CTAs per SM at 96 registers)
+    int cells[3] = {vol->ndim == 3 ? 2 : 10, vol->ndim == 3 ? 2 : 8, 2};
+    auto brick_of = [&](int d) {
+        const int b = p->brick[d] ? p->brick[d] : (int)std::lround(cells[d] * stride_hint / vol->sp[d]);
+        return std::max(1, std::min(b, (int)std::min<int64_t>(vol->n[d], 224)));
+    };
     for (int d = 0; d < vol->ndim; ++d) {
-        // lattice cells per brick: 2x2x2 in 3D, 10x8 in 2D (measured best for 128
-        // samples: 80 contours of 4 lanes fill 10 warps, two CTAs per SM at 96 registers)
-        const double cells = vol->ndim == 3 ? 2.0 : (d == 0 ? 10.0 : 8.0);
-        B[d] = p->brick[d] ? p->brick[d] : (int)std::lround(cells * stride_hint / vol->sp[d]);
-        B[d] = std::max(1, std::min(B[d], (int)std::min<int64_t>(vol->n[d], 224)));
+        B[d] = brick_of(d);
         const double hf = p->halo_factor > 0.0f ? p->halo_factor : (vol->ndim == 3 ? 2.5 : 3.5);
         h[d] = (int)std::ceil((hf * r_hint + 0.5 * p->dR) / vol->sp[d]) + 2;
+    }
+    if (!p->brick[0] && !p->brick[1] && !p->brick[2]) {
+        // a small volume gets more, smaller bricks (down to 2 cells per axis in 2D, 1 in
+        // 3D), so that the grid holds about four CTAs per slot (152 SMs x 2) instead of
+        // a tail wave
+        auto n_bricks = [&]() {
+            int64_t nb = 1;
+            for (int d = 0; d < vol->ndim; ++d) nb *= (vol->n[d] + B[d] - 1) / B[d];
+            return nb;
+        };
+        const int min_cells = vol->ndim == 3 ? 1 : 2;
+        while (n_bricks() < 1216) {
+            int dm = -1;
+            for (int d = 0; d < vol->ndim; ++d)
+                if (cells[d] > min_cells && (dm < 0 || cells[d] > cells[dm])) dm = d;
+            if (dm < 0) break;
+            cells[dm] = std::max(min_cells, cells[dm] / 2);
+            B[dm] = brick_of(dm);
+        }
     }
     for (int iter = 0; iter < 4096; ++iter) {
         int64_t raw = vol->es;
@@ -537,11 +559,11 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
             pl.quad_off = (int)quad_off;
             pl.smem = (int)total;
             if (p->warps_per_block == 0) {
-                // enough groups for the contours of a brick (lattice estimate), 2..8 warps
+                // enough groups for the contours of a brick (lattice estimate), 1..16 warps
                 double per = 1.0;
                 for (int d = 0; d < vol->ndim; ++d) per *= std::max(1.0, B[d] * (double)vol->sp[d] / stride_hint);
                 const int w = (int)std::ceil(per * G / 32.0);
-                pl.warps = std::max(2, std::min(16, w));
+                pl.warps = std::max(1, std::min(16, w));
             }
             return AC_OK;
         }
