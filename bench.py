@@ -359,9 +359,11 @@ def main(argv=None):
     # end to end through the C ABI from pinned host memory
     e2e = None
     if not args.no_e2e:
-        e2e_ms = []
+        e2e_ms, e2e_kms = [], []
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
+        eclocks = ClockSampler(uuid)
+        eclocks.start()
         for i in range(args.steps):
             flush.zero_()
             b0.record()
@@ -369,9 +371,12 @@ def main(argv=None):
             b1.record()
             b1.synchronize()
             e2e_ms.append(b0.elapsed_time(b1))
+            e2e_kms.append(ac.ac_evolve_kernel_ms(C))
+        eclk = eclocks.stop()
         e_ms, e_val = aggregate_ranks(e2e_ms, samples, world, reducer)
         e2e = {"value": e_val, "unit": "samples/s", "ms_per_step": e_ms,
-               "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(len(cells) * 24 + 4 * 6)}
+               "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(len(cells) * 24 + 4 * 6),
+               "evolve_kernel_ms": float(np.mean(e2e_kms)), "clocks": eclk}
 
     achieved = ALG_SLOTS_PER_SAMPLE[ndim] * samples / (k_ms * 1e-3) / 1e12
     peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
