@@ -41,17 +41,18 @@ import numpy as np  # noqa: E402
 # one sample -- Philox4x32-10 (10 rounds of two wide multiplies and two three-input
 # XORs per block), word-to-float conversions, radius and direction (hardware
 # sqrt / lg2+ex2 / sin / cos), index offsets, floor and fraction per axis, the
-# gather and multilinear interpolation, the two weight bands, and compensated
-# accumulation of the four (2D) or five (3D) sums.  2D: 76 (a Philox block serves
-# two samples; one quad load per bilinear gather); 3D: 147 (one block per
-# sample; eight 8/16-bit taps with exact integer-to-float conversion).  The
-# per-iteration reduction and update are excluded.
-ALG_SLOTS_PER_SAMPLE = {2: 76.0, 3: 147.0}
+# gather and multilinear interpolation, the two weight bands, and the sums (one
+# product and one pairwise addition per sum, and a four-operation compensated step
+# per block of B samples).  2D: 65.5 (a Philox block serves two samples; one
+# quad load of values and x-differences per bilinear gather; B = 8); 3D: 124.75
+# (three blocks per four samples; eight 8/16-bit taps, each one operation from
+# exact biased floats, four bases unbiased; B = 4).  The per-iteration reduction
+# and update are excluded.
+ALG_SLOTS_PER_SAMPLE = {2: 65.5, 3: 124.75}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
-# ncu capture of the current kernel (to be removed when the kernel changes), scaled
-# with the volume and contour count: the 2048^2 instance of large-2d read 7.05 MB
-# (x 4), the 256x256x64 instance of brain-3d 9.51 MB (x 64).
-DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.2e6, ("brain-3d", "brick", 0, "native"): 608.3e6}
+# ncu capture of the current kernel, scaled with the volume and contour count; empty
+# while the kernel has changed since its last capture.
+DRAM_BYTES_PER_LAUNCH = {}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0

@@ -15,8 +15,8 @@
  * `hbm_budget_bytes`, and tiles that finished are localized, their cells kept for
  * the caller, and their device memory released (a tile is admitted when it fits
  * the byte budget, the tile cap and the contour cap; the first tile in line is
- * always admitted when nothing is resident).  Because the Philox counter of a
- * sample is (j, n, k, stream_id) with one key for the server, a tile's cells and
+ * always admitted when nothing is resident).  Because the Philox counters of a
+ * sample are (block, n, k, stream_id) with one key for the server, a tile's cells and
  * energies do not depend on which tiles it shared rounds with: they equal those
  * of ac_evolve on that tile alone with the server's evolve parameters and the
  * tile's stream_id.

@@ -34,10 +34,13 @@
  *   - d = 3 in 3D (alpha = 3, Eq. 4) and d = 2 in 2D (the same symmetric-slope
  *     argument gives alpha = 2 for disks);
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
- *     (sample, iteration, contour, stream) and key (seed_lo, seed_hi); a uniform is
- *     (w >> 8) * 2^-24; 3D ball point = cbrt(u0) (sin phi cos th, sin phi sin th,
- *     cos phi) with cos phi = 1 - 2 u1, th = 2 pi u2; 2D disk point follows the
- *     paper's (sqrt(u) cos th, sqrt(u) sin th), two samples per Philox block;
+ *     (block, iteration, contour, stream) and key (seed_lo, seed_hi); the words of
+ *     one iteration and contour form the stream block 0, block 1, ... (four words
+ *     each) and sample j takes words d j .. d j + d - 1 (2D: one block per two
+ *     samples; 3D: three blocks per four samples); a uniform is (w >> 8) * 2^-24;
+ *     3D ball point = cbrt(u0) (sin phi cos th, sin phi sin th, cos phi) with
+ *     cos phi = 1 - 2 u1, th = 2 pi u2; 2D disk point follows the paper's
+ *     (sqrt(u0) cos th, sqrt(u0) sin th), th = 2 pi u1;
  *   - clamps that the paper does not state: |dc| <= max_step, |dR| <= max_step,
  *     R in [Rmin, Rmax], c inside the box of voxel centres;
  *   - T iterations = T evaluations; the update follows evaluations 1..T-1, so the
@@ -86,7 +89,8 @@ double or_uniform24(uint32_t w)
 
 /* Uniform point in the unit ball (ndim 3) or unit disk (ndim 2).  For the disk,
  * `which` selects the first (words 0,1) or second (words 2,3) sample of the block. */
-void or_unit_sample(int ndim, const uint32_t w[4], int which, double u[3])
+/* The unit-ball (disk) point of one sample from its ndim random words. */
+void or_unit_sample(int ndim, const uint32_t w[3], double u[3])
 {
     if (ndim == 3) {
         double rad = cbrt(or_uniform24(w[0]));
@@ -97,8 +101,8 @@ void or_unit_sample(int ndim, const uint32_t w[4], int which, double u[3])
         u[1] = rad * sphi * sin(th);
         u[2] = rad * cphi;
     } else {
-        double r = or_uniform24(w[2 * which]);
-        double th = 2.0 * OR_PI * or_uniform24(w[2 * which + 1]);
+        double r = or_uniform24(w[0]);
+        double th = 2.0 * OR_PI * or_uniform24(w[1]);
         u[0] = sqrt(r) * cos(th);
         u[1] = sqrt(r) * sin(th);
         u[2] = 0.0;
@@ -259,6 +263,25 @@ static void sample_block(const or_params *P, int64_t blk, int64_t iter, int64_t 
     or_philox4x32_10(ctr, P->key, w);
 }
 
+/* Reader of the word stream of one (iteration, contour): word m is word m % 4 of
+ * block m / 4; the last block drawn is kept. */
+typedef struct {
+    int64_t blk;
+    uint32_t w[4];
+} word_stream;
+
+static void sample_words(const or_params *P, word_stream *S, int64_t j, int64_t iter, int64_t k, uint32_t out[3])
+{
+    for (int t = 0; t < P->ndim; ++t) {
+        const int64_t m = (int64_t)P->ndim * j + t;
+        if (m / 4 != S->blk) {
+            S->blk = m / 4;
+            sample_block(P, S->blk, iter, k, S->w);
+        }
+        out[t] = S->w[m % 4];
+    }
+}
+
 /* Running sums over the points of K for one evaluation: the weighted sums of S I
  * and of the partials of S with respect to p and q times I (Eqs. 5, 7-10), the
  * magnitude sums that scale the parity tolerances, and raw moments of the
@@ -370,16 +393,12 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
     band_edges(P, R, edges);
     or_sums A;
     memset(&A, 0, sizeof(A));
-    uint32_t w[4];
+    word_stream S = {-1, {0, 0, 0, 0}};
+    uint32_t w[3];
     for (int64_t j = 0; j < P->N; ++j) {
         double u[3], x[3];
-        if (d == 3) {
-            sample_block(P, j, iter, k, w);
-            or_unit_sample(3, w, 0, u);
-        } else {
-            sample_block(P, j / 2, iter, k, w);
-            or_unit_sample(2, w, (int)(j & 1), u);
-        }
+        sample_words(P, &S, j, iter, k, w);
+        or_unit_sample(d, w, u);
         for (int a = 0; a < 3; ++a) x[a] = c[a] + Ro * u[a];
         if (d == 2) x[2] = c[2];
         add_point(&A, P, c, R, edges, x, or_image_value(img, x), wmc);
@@ -684,15 +703,11 @@ void or_image_values(const or_image *img, int64_t n, const double *x, double *ou
  * drawn exactly as or_eval_pq draws them. */
 void or_unit_samples(const or_params *P, int64_t iter, int64_t k, double *out)
 {
-    uint32_t w[4];
+    word_stream S = {-1, {0, 0, 0, 0}};
+    uint32_t w[3];
     for (int64_t j = 0; j < P->N; ++j) {
-        if (P->ndim == 3) {
-            sample_block(P, j, iter, k, w);
-            or_unit_sample(3, w, 0, out + 3 * j);
-        } else {
-            sample_block(P, j / 2, iter, k, w);
-            or_unit_sample(2, w, (int)(j & 1), out + 3 * j);
-        }
+        sample_words(P, &S, j, iter, k, w);
+        or_unit_sample(P->ndim, w, out + 3 * j);
     }
 }
 

@@ -106,15 +106,27 @@ __device__ __forceinline__ void fast_axis(float x, float M, int &idx, float &fr)
     idx = (int)__float_as_uint(t) - 0x4B000000;
 }
 
-// 2D region as quads (v[y][x], v[y][x+1], v[y+1][x], v[y+1][x+1]): four halves
-// (8 bytes) for uint8 and binary16 voxels, which half precision holds exactly,
-// float4 otherwise.  One shared-memory load feeds a bilinear sample.
+// 2D region as quads: one shared-memory load feeds a bilinear sample.  With
+// `diff`, a quad holds (v00, v10 - v00, v01, v11 - v01), the x-differences the
+// interpolation needs (computed once per quad in FP32, as the sample would); else
+// (v00, v10, v01, v11).  Four halves (8 bytes) for uint8 voxels (values and
+// differences are integers below 2^9, exact in half precision) and binary16 voxels
+// (values only: their differences need not be representable), float4 otherwise.
 struct HQuad {
-    __half2 lo, hi;   // (v00, v10), (v01, v11)
+    __half2 lo, hi;
 };
-template <typename T> struct QuadOf { using type = float4; };
-template <> struct QuadOf<uint8_t> { using type = HQuad; };
-template <> struct QuadOf<__half> { using type = HQuad; };
+template <typename T> struct QuadOf {
+    using type = float4;
+    static constexpr bool diff = true;
+};
+template <> struct QuadOf<uint8_t> {
+    using type = HQuad;
+    static constexpr bool diff = true;
+};
+template <> struct QuadOf<__half> {
+    using type = HQuad;
+    static constexpr bool diff = false;
+};
 
 __device__ __forceinline__ float4 quad_f(const float4 &q) { return q; }
 __device__ __forceinline__ float4 quad_f(const HQuad &q)
@@ -132,13 +144,13 @@ template <> __device__ __forceinline__ HQuad make_quad<HQuad>(float a, float b, 
     return HQuad{__floats2half2_rn(a, b), __floats2half2_rn(c, d)};
 }
 
-__device__ __forceinline__ float quad_lerp(const float4 q, float f0, float f1)
+template <bool DIFF> __device__ __forceinline__ float quad_lerp(const float4 q, float f0, float f1)
 {
-    const float a0 = fmaf(f0, q.y - q.x, q.x), a1 = fmaf(f0, q.w - q.z, q.z);
+    const float a0 = fmaf(f0, DIFF ? q.y : q.y - q.x, q.x), a1 = fmaf(f0, DIFF ? q.w : q.w - q.z, q.z);
     return fmaf(f1, a1 - a0, a0);
 }
 
-template <typename QT> struct QuadFast {
+template <typename QT, bool DIFF> struct QuadFast {
     const QT *Q;
     int qp;          // quads per row
     float M[2];
@@ -150,40 +162,47 @@ template <typename QT> struct QuadFast {
         float f0, f1;
         fast_axis(x0, M[0], i0, f0);
         fast_axis(x1, M[1], i1, f1);
-        return quad_lerp(quad_f(Q[checked(i1 * qp + i0, nq, st)]), f0, f1);
+        return quad_lerp<DIFF>(quad_f(Q[checked(i1 * qp + i0, nq, st)]), f0, f1);
     }
 };
 
-// Bilinear / trilinear from four / eight taps of a raw array at q.
+// Bilinear / trilinear from four / eight taps of a raw array at q.  The loader
+// returns biased taps for integer voxels (TapBias); differences are exact either
+// way and only the base of each x-interpolation is unbiased, which gives the same
+// bits as converting every tap.
 template <int DIM, typename T, typename LD>
 __device__ __forceinline__ float interp(const T *q, int64_t py, int64_t pz, float f0, float f1, float f2, LD ld)
 {
+    constexpr float Z = LD::bias;
     const float v00 = ld(q), v10 = ld(q + 1), v01 = ld(q + py), v11 = ld(q + py + 1);
-    const float a0 = fmaf(f0, v10 - v00, v00), a1 = fmaf(f0, v11 - v01, v01);
+    const float a0 = fmaf(f0, v10 - v00, v00 - Z), a1 = fmaf(f0, v11 - v01, v01 - Z);
     const float s0 = fmaf(f1, a1 - a0, a0);
     if (DIM == 2) return s0;
     const T *r = q + pz;
     const float w00 = ld(r), w10 = ld(r + 1), w01 = ld(r + py), w11 = ld(r + py + 1);
-    const float b0 = fmaf(f0, w10 - w00, w00), b1 = fmaf(f0, w11 - w01, w01);
+    const float b0 = fmaf(f0, w10 - w00, w00 - Z), b1 = fmaf(f0, w11 - w01, w01 - Z);
     const float s1 = fmaf(f1, b1 - b0, b0);
     return fmaf(f2, s1 - s0, s0);
 }
 
-// Tap loaders; base, n and st serve the checked build only.
+// Tap loaders (biased taps for integer voxels, see interp); base, n and st serve
+// the checked build only.
 template <typename T> struct SmemLoad {
+    static constexpr float bias = TapBias<T>::value;
     const T *base;
     int64_t n;
     int32_t *st;
     __device__ __forceinline__ float operator()(const T *p) const
     {
 #ifdef AC_CHECKED
-        return to_f<T>(base[checked((int64_t)(p - base), n, st)]);
+        return to_biased<T>(base[checked((int64_t)(p - base), n, st)]);
 #else
-        return to_f<T>(*p);
+        return to_biased<T>(*p);
 #endif
     }
 };
 template <typename T> struct GlobalLoad {
+    static constexpr float bias = 0.0f;
     const T *base;
     int64_t n;
     int32_t *st;
@@ -232,7 +251,7 @@ template <int DIM, typename T, bool QUAD> struct SmemClamp {
         if (QUAD) {
             using QT = typename QuadOf<T>::type;
             const int64_t qi = checked((int64_t)(o[1] + b1) * py + (o[0] + b0), n, st);
-            return quad_lerp(quad_f(reinterpret_cast<const QT *>(p)[qi]), f0, f1);
+            return quad_lerp<QuadOf<T>::diff>(quad_f(reinterpret_cast<const QT *>(p)[qi]), f0, f1);
         }
         const T *q = reinterpret_cast<const T *>(p) + (o[0] + b0) + (o[1] + b1) * py + (DIM == 3 ? (o[2] + b2) * pz : 0);
         return interp<DIM, T>(q, py, pz, f0, f1, f2, SmemLoad<T>{reinterpret_cast<const T *>(p), n, st});
@@ -274,12 +293,12 @@ __device__ __forceinline__ Terms sample_terms(const IterC<DIM> &ic, const Evolve
     const float t1 = fmaf(rv, ic.A1, ic.B1), t2 = fmaf(rv, ic.A2, ic.B2);
     const float r1 = __saturatef(t1), r2 = __saturatef(t2);
     const float S = fmaf(2.0f, r1, -1.0f) - r2;
-    const bool b1 = r1 == t1, b2 = r2 == t2;   // sample inside the inner / outer band
-    const float dSdR = (b1 ? a.kR1 : 0.0f) + (b2 ? a.kR2 : 0.0f);
-    const float g = ((b1 ? a.kr1 : 0.0f) + (b2 ? a.kr2 : 0.0f)) * I;
+    // I where the sample lies inside the inner / outer band (slopes there), else 0
+    const float m1 = r1 == t1 ? I : 0.0f, m2 = r2 == t2 ? I : 0.0f;
+    const float g = fmaf(a.kr1, m1, a.kr2 * m2);
     Terms t;
     t.v[0] = S * I;
-    t.v[1] = dSdR * I;
+    t.v[1] = fmaf(a.kR1, m1, a.kR2 * m2);
     t.v[2] = g * d0;
     t.v[3] = g * d1;
     t.v[4] = DIM == 3 ? g * d2 : 0.0f;
@@ -320,10 +339,22 @@ __device__ __forceinline__ void add_terms4(KSum *acc, const Terms &x, const Term
     }
 }
 
+// Pairwise sum of four samples, kept to be joined with the next four.
+template <int DIM> __device__ __forceinline__ Terms sum4(const Terms &x, const Terms &y, const Terms &z, const Terms &w)
+{
+    Terms h;
+#pragma unroll
+    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) h.v[i] = (x.v[i] + y.v[i]) + (z.v[i] + w.v[i]);
+    return h;
+}
+
 // All samples of one contour-iteration handled by this lane (lane `lig` of G).
-// 3D: sample j uses Philox block (j, n, k, stream): radius cbrt(u0), cos(phi) =
-// 1 - 2 u1, azimuth 2 pi u2.  2D: block m gives samples 2m and 2m+1, radius
-// sqrt(u), azimuth 2 pi u' ("Monte-Carlo Integration" section).  ACC selects
+// The words of iteration n of contour k form the stream Philox(0, n, k, stream),
+// Philox(1, n, k, stream), ... (four words per block) and sample j takes words
+// d j .. d j + d - 1.  3D: the quad of samples 4q .. 4q + 3 takes blocks 3q,
+// 3q + 1, 3q + 2; radius cbrt(u0), cos(phi) = 1 - 2 u1, azimuth 2 pi u2.  2D:
+// block m gives samples 2m and 2m + 1; radius sqrt(u0), azimuth 2 pi u1
+// ("Monte-Carlo Integration" section).  ACC selects
 // correctly rounded sqrt / cbrt and the polynomial sine and cosine (used when few
 // samples make per-sample accuracy visible); otherwise the hardware
 // approximations.
@@ -341,17 +372,16 @@ __device__ __forceinline__ void raw_direction2(uint32_t wa, float &d0, float &d1
 }
 
 template <int DIM, bool ACC, typename Gather>
-__device__ __forceinline__ Terms sample3(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a, uint32_t j,
-                                         uint32_t n, uint32_t k, uint32_t stream)
+__device__ __forceinline__ Terms sample3(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a, uint32_t w0,
+                                         uint32_t w1, uint32_t w2)
 {
-    const uint4 w = philox4x32_10(make_uint4(j, n, k, stream), a.rk0, a.rk1);
-    const float u0 = top24(w.x) * 5.9604644775390625e-8f;
+    const float u0 = top24(w0) * 5.9604644775390625e-8f;
     const float rv = ACC ? cbrtf(u0) : ex2_approx(lg2_approx(u0) * (1.0f / 3.0f));
-    const float t = top24(w.y) * 5.9604644775390625e-8f;
+    const float t = top24(w1) * 5.9604644775390625e-8f;
     const float cphi = fmaf(-2.0f, t, 1.0f);
     const float sh = ACC ? sqrtf(t * (1.0f - t)) : sqrt_approx(t * (1.0f - t));
     float c0, s0;
-    raw_direction2<DIM, ACC>(w.z, c0, s0);
+    raw_direction2<DIM, ACC>(w2, c0, s0);
     const float d0 = sh * c0, d1 = sh * s0;
     const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
     const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
@@ -376,27 +406,53 @@ __device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DI
                                                uint32_t n, uint32_t k, uint32_t stream, int lig, KSum *acc)
 {
     if constexpr (DIM == 3) {
-        // samples j, j + G, j + 2G, j + 3G of this lane are computed together (more
-        // independent work per warp) and summed in two roundings before one
-        // compensated addition; the rest go in pairs
-        int j = lig;
-        for (; j + 3 * G < a.N; j += 4 * G) {
-            add_terms4<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, (uint32_t)j, n, k, stream),
-                                  sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + G), n, k, stream),
-                                  sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + 2 * G), n, k, stream),
-                                  sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + 3 * G), n, k, stream));
+        // a lane takes quads q, q + G, ...: three Philox blocks give its four
+        // samples, summed in two roundings before one compensated addition; the
+        // last N mod 4 samples (the start of quad N / 4) go to one lane
+        const int nq = a.N >> 2;
+        int q = lig;
+#pragma unroll 1
+        for (; q < nq; q += G) {
+            const uint4 A = philox4x32_10(make_uint4((uint32_t)(3 * q), n, k, stream), a.rk0, a.rk1);
+            const uint4 B = philox4x32_10(make_uint4((uint32_t)(3 * q + 1), n, k, stream), a.rk0, a.rk1);
+            const uint4 C = philox4x32_10(make_uint4((uint32_t)(3 * q + 2), n, k, stream), a.rk0, a.rk1);
+            add_terms4<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y, A.z),
+                                  sample3<DIM, ACC>(gat, ic, a, A.w, B.x, B.y),
+                                  sample3<DIM, ACC>(gat, ic, a, B.z, B.w, C.x),
+                                  sample3<DIM, ACC>(gat, ic, a, C.y, C.z, C.w));
         }
-        for (; j < a.N; j += 2 * G) {
-            const Terms x = sample3<DIM, ACC>(gat, ic, a, (uint32_t)j, n, k, stream);
-            if (j + G < a.N) add_terms<DIM, COMP>(acc, x, sample3<DIM, ACC>(gat, ic, a, (uint32_t)(j + G), n, k, stream));
-            else add_terms<DIM, COMP>(acc, x);
+        const int rem = a.N & 3;
+        if (rem && lig == nq % G) {
+            const uint4 A = philox4x32_10(make_uint4((uint32_t)(3 * nq), n, k, stream), a.rk0, a.rk1);
+            add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y, A.z));
+            if (rem > 1) {
+                const uint4 B = philox4x32_10(make_uint4((uint32_t)(3 * nq + 1), n, k, stream), a.rk0, a.rk1);
+                add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.w, B.x, B.y));
+                if (rem > 2) {
+                    const uint4 C = philox4x32_10(make_uint4((uint32_t)(3 * nq + 2), n, k, stream), a.rk0, a.rk1);
+                    add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, B.z, B.w, C.x));
+                }
+            }
         }
     } else {
-        // the two samples of a Philox block form a pair; two blocks of a lane (m and
-        // m + G) are summed together; a leftover block and an odd N's last sample
-        // are handled after the loop
+        // the two samples of a Philox block form a pair; four blocks of a lane (m,
+        // m + G, m + 2G, m + 3G) are summed pairwise in three roundings before one
+        // compensated addition, then two blocks, then a leftover block and an odd
+        // N's last sample
         const int pairs = a.N >> 1;
         int m = lig;
+#pragma unroll 1
+        for (; m + 3 * G < pairs; m += 4 * G) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
+            const uint4 u = philox4x32_10(make_uint4((uint32_t)(m + G), n, k, stream), a.rk0, a.rk1);
+            const Terms h = sum4<DIM>(sample2<DIM, ACC>(gat, ic, a, w.x, w.y), sample2<DIM, ACC>(gat, ic, a, w.z, w.w),
+                                      sample2<DIM, ACC>(gat, ic, a, u.x, u.y), sample2<DIM, ACC>(gat, ic, a, u.z, u.w));
+            const uint4 w2 = philox4x32_10(make_uint4((uint32_t)(m + 2 * G), n, k, stream), a.rk0, a.rk1);
+            const uint4 u2 = philox4x32_10(make_uint4((uint32_t)(m + 3 * G), n, k, stream), a.rk0, a.rk1);
+            const Terms q = sum4<DIM>(sample2<DIM, ACC>(gat, ic, a, w2.x, w2.y), sample2<DIM, ACC>(gat, ic, a, w2.z, w2.w),
+                                      sample2<DIM, ACC>(gat, ic, a, u2.x, u2.y), sample2<DIM, ACC>(gat, ic, a, u2.z, u2.w));
+            add_terms<DIM, COMP>(acc, h, q);
+        }
 #pragma unroll 1
         for (; m + G < pairs; m += 2 * G) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
@@ -609,7 +665,9 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
         for (int i = threadIdx.x; i < nq; i += blockDim.x) {
             const int y = i / qp, x = i - y * qp;
             const T *r = reg + y * a.ext[0] + x;
-            Q[i] = make_quad<QT>(to_f<T>(r[0]), to_f<T>(r[1]), to_f<T>(r[a.ext[0]]), to_f<T>(r[a.ext[0] + 1]));
+            const float v00 = to_f<T>(r[0]), v10 = to_f<T>(r[1]);
+            const float v01 = to_f<T>(r[a.ext[0]]), v11 = to_f<T>(r[a.ext[0] + 1]);
+            Q[i] = QuadOf<T>::diff ? make_quad<QT>(v00, v10 - v00, v01, v11 - v01) : make_quad<QT>(v00, v10, v01, v11);
         }
         __syncthreads();
     }
@@ -655,7 +713,7 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
             if (inside && interior) {
                 const float M[3] = {8388608.0f + (float)o[0], 8388608.0f + (float)o[1], 8388608.0f + (float)o[2]};
                 if (quad) {
-                    QuadFast<QT> gat{Q, qp, {M[0], M[1]}, nquads, V.status};
+                    QuadFast<QT, QuadOf<T>::diff> gat{Q, qp, {M[0], M[1]}, nquads, V.status};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 } else {
                     RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}, nraw, V.status};

@@ -228,11 +228,30 @@ template <> __device__ __forceinline__ float to_f<uint16_t>(uint16_t v)
 template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
 
+// Integer taps as biased floats 2^23 + v (exact, one bitwise or): the difference of
+// two biased taps is exact, so an interpolation converts only its base tap.
+template <typename T> struct TapBias {
+    static constexpr float value = 0.0f;
+};
+template <> struct TapBias<uint8_t> {
+    static constexpr float value = 8388608.0f;
+};
+template <> struct TapBias<uint16_t> {
+    static constexpr float value = 8388608.0f;
+};
+template <typename T> __device__ __forceinline__ float to_biased(T v) { return to_f<T>(v); }
+template <> __device__ __forceinline__ float to_biased<uint8_t>(uint8_t v) { return __uint_as_float(0x4B000000u | v); }
+template <> __device__ __forceinline__ float to_biased<uint16_t>(uint16_t v) { return __uint_as_float(0x4B000000u | v); }
+
 template <typename T> __device__ __forceinline__ float ldg_f(const T *p) { return to_f<T>(__ldg(p)); }
 template <> __device__ __forceinline__ float ldg_f<__half>(const __half *p)
 {
     return __half2float(__ldg(reinterpret_cast<const __half *>(p)));
 }
+// biased load (integer voxels), plain load otherwise
+template <typename T> __device__ __forceinline__ float ldg_biased(const T *p) { return ldg_f<T>(p); }
+template <> __device__ __forceinline__ float ldg_biased<uint8_t>(const uint8_t *p) { return to_biased<uint8_t>(__ldg(p)); }
+template <> __device__ __forceinline__ float ldg_biased<uint16_t>(const uint16_t *p) { return to_biased<uint16_t>(__ldg(p)); }
 
 // ----------------------------------------------------------------- compensated sums
 // Kahan accumulation per lane; value = s - c.

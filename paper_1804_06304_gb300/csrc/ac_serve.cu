@@ -2,7 +2,7 @@
 // thread.  The loop is a client of the library's own C ABI (volumes, lattice
 // seeding, a plan over the resident tiles with per-tile iteration windows, and
 // localization), so a tile evolves exactly as it would alone: the sample
-// counters are (j, n, k, stream_id) under the server's single Philox key, and the
+// counters are (block, n, k, stream_id) under the server's single Philox key, and the
 // lane grouping depends only on the evolve parameters, never on the mix.
 #include <cuda_runtime.h>
 

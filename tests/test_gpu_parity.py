@@ -441,8 +441,8 @@ def test_empty_set_and_single_iteration(ac, small3d):
 @pytest.mark.parametrize("path", [0, 1, 2])
 def test_integer_translation_invariance_on_gpu(ac, small3d, path):
     """Shifting image and seeds by whole voxels leaves energies and trajectories
-    unchanged up to FP32 rounding of the positions (the Philox counter depends only
-    on (j, n, k, stream)); at least 95% of the contours agree to 2e-4 voxel."""
+    unchanged up to FP32 rounding of the positions (the Philox counters depend only
+    on (block, n, k, stream)); at least 95% of the contours agree to 2e-4 voxel."""
     s = small3d
     shift = np.array([7.0, 5.0, 3.0])
     big = np.zeros((s.volume.shape[0] + 6, s.volume.shape[1] + 10, s.volume.shape[2] + 14), np.uint8)

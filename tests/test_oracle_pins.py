@@ -95,6 +95,31 @@ def test_unit_ball_sampling_is_uniform(oracle, ndim):
         assert np.all(u[:, :2] == u[:, :2])  # finite
 
 
+@pytest.mark.parametrize("ndim,N", [(3, 67), (2, 33)])
+def test_sample_word_layout(oracle, ndim, N):
+    """Sample j takes words d j .. d j + d - 1 of the stream Philox(0, n, k, s),
+    Philox(1, n, k, s), ...: radius, polar and azimuth angles follow from those words
+    alone (3D: three blocks per four samples; 2D: one block per two)."""
+    it, k, sid = 4, 9, 2
+    P = oracle.make_params(ndim, N, seed=0x1234567890ABCDEF, stream_id=sid)
+    nb = (ndim * N + 3) // 4
+    ctr = np.array([[b, it, k, sid] for b in range(nb)], dtype=np.uint32)
+    words = oracle.philox(ctr, [0x90ABCDEF, 0x12345678]).reshape(-1)
+    u = oracle.unit_samples(P, it, k)
+    for j in range(N):
+        w = [int(x) for x in words[ndim * j: ndim * j + ndim]]
+        r = np.linalg.norm(u[j, :ndim])
+        if ndim == 3:
+            assert r == pytest.approx(oracle.uniform24(w[0]) ** (1 / 3), rel=1e-12, abs=1e-12)
+            assert u[j, 2] == pytest.approx(r * (1 - 2 * oracle.uniform24(w[1])), abs=1e-12)
+        else:
+            assert r == pytest.approx(math.sqrt(oracle.uniform24(w[0])), rel=1e-12, abs=1e-12)
+        if r > 1e-6 and np.hypot(u[j, 0], u[j, 1]) > 1e-9:
+            th = math.atan2(u[j, 1], u[j, 0]) % (2 * math.pi)
+            want = 2 * math.pi * oracle.uniform24(w[ndim - 1])
+            assert min(abs(th - want), 2 * math.pi - abs(th - want)) < 1e-9
+
+
 def test_counter_layout_distinct_streams(oracle):
     """Different contour index / iteration / stream give different samples."""
     P = oracle.make_params(3, 64, seed=3)
