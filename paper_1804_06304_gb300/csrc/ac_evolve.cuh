@@ -588,8 +588,8 @@ __device__ __forceinline__ Step eval_contour(const Gather &gat, const IterC<DIM>
     KSum acc[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
     sample_contour<DIM, G, COMP, ACC>(gat, ic, a, (uint32_t)n, k, stream, lig, acc);
     float sums[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) sums[i] = (DIM == 2 && i == 4) ? 0.0f : group_reduce<G, COMP>(acc[i], mask);
+    sums[4] = 0.0f;
+    group_reduce_all<G, COMP, DIM == 3 ? 5 : 4>(acc, sums, mask);
     return finish<DIM>(sums, R, a, scale);
 }
 

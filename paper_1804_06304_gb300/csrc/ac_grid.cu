@@ -91,8 +91,8 @@ __device__ __forceinline__ Step eval_grid(const VolDesc &V, const EvolveArgs &a,
         }
     }
     float sums[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) sums[m] = (DIM == 2 && m == 4) ? 0.0f : group_reduce<G, COMP>(acc[m], mask);
+    sums[4] = 0.0f;
+    group_reduce_all<G, COMP, DIM == 3 ? 5 : 4>(acc, sums, mask);
     // Eqs. 5-11 in centre/radius form with the voxel volume as the measure
     float vox = V.sp[0] * V.sp[1];
     if (DIM == 3) vox *= V.sp[2];

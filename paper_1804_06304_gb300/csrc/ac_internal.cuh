@@ -266,29 +266,92 @@ __device__ __forceinline__ void kadd(KSum &a, float x)
     a.s = t;
 }
 
-// Butterfly reduction over G lanes.  Compensated: (s, e) pairs combined with the
-// exact TwoSum error; every lane of the group ends with the same bits.
-template <int G, bool COMP>
-__device__ __forceinline__ float group_reduce(KSum a, unsigned mask)
+// Reduction of K sums over G lanes by recursive halving: at each level (offset
+// OFF) a lane keeps half of the partial sums it still holds -- the lower half
+// where lane bit OFF is clear, the upper half where it is set -- and receives the
+// partner's values of those, so each level exchanges about half as many values as
+// the one before; once a lane holds one sum, each remaining level halves the lanes
+// that hold it.  Compensated: (s, e) pairs combined with the exact TwoSum error.
+// Sum i ends at a lane and position fixed at compile time and is broadcast from
+// there, so every lane of the group ends with the same bits.
+__device__ __forceinline__ void pair_add(float &s, float &e, float os, float oe)
 {
-    if (!COMP) {
-        float s = a.s;
+    const float t = s + os;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (os - bp);
+    e = (e + oe) + err;
+    s = t;
+}
+
+template <int OFF, int N, bool COMP>
+__device__ __forceinline__ void halve_level(float *s, float *e, unsigned lane, unsigned mask)
+{
+    if constexpr (OFF > 0) {
+        constexpr int M = (N + 1) / 2;
+        const bool up = (lane & OFF) != 0;
 #pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(mask, s, off);
-        return s;
+        for (int j = 0; j < M; ++j) {
+            const float hs = (M + j < N) ? s[M + j] : 0.0f;
+            const float he = (COMP && M + j < N) ? e[M + j] : 0.0f;
+            const float ks = up ? hs : s[j], xs = up ? s[j] : hs;
+            const float ke = up ? he : e[j], xe = up ? e[j] : he;
+            const float rs = __shfl_xor_sync(mask, xs, OFF);
+            if (COMP) {
+                const float re = __shfl_xor_sync(mask, xe, OFF);
+                s[j] = ks;
+                e[j] = ke;
+                pair_add(s[j], e[j], rs, re);
+            } else {
+                s[j] = ks + rs;
+            }
+        }
+        halve_level<OFF / 2, M, COMP>(s, e, lane, mask);
     }
-    float s = a.s, e = -a.c;
-#pragma unroll
+}
+
+// Lane (within the group) and position where sum i ends.
+template <int G, int K> __host__ __device__ constexpr int reduce_owner(int i)
+{
+    int n = K, p = i, lane = 0;
     for (int off = G / 2; off > 0; off >>= 1) {
-        const float os = __shfl_xor_sync(mask, s, off);
-        const float oe = __shfl_xor_sync(mask, e, off);
-        const float t = s + os;
-        const float bp = t - s;
-        const float err = (s - (t - bp)) + (os - bp);
-        e = (e + oe) + err;
-        s = t;
+        const int m = (n + 1) / 2;
+        if (p >= m) {
+            p -= m;
+            lane |= off;
+        }
+        n = m;
     }
-    return s + e;
+    return lane;
+}
+template <int G, int K> __host__ __device__ constexpr int reduce_pos(int i)
+{
+    int n = K, p = i;
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const int m = (n + 1) / 2;
+        if (p >= m) p -= m;
+        n = m;
+    }
+    return p;
+}
+
+template <int G, bool COMP, int K>
+__device__ __forceinline__ void group_reduce_all(const KSum *acc, float *out, unsigned mask)
+{
+    float s[K], e[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        s[i] = acc[i].s;
+        e[i] = COMP ? -acc[i].c : 0.0f;
+    }
+    const unsigned lane = threadIdx.x & 31u;
+    halve_level<G / 2, K, COMP>(s, e, lane, mask);
+    const int base = (int)(lane & ~(unsigned)(G - 1));
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int pos = reduce_pos<G, K>(i);
+        const float v = COMP ? s[pos] + e[pos] : s[pos];
+        out[i] = __shfl_sync(mask, v, base + reduce_owner<G, K>(i));
+    }
 }
 
 // ----------------------------------------------------------------- per-contour setup
