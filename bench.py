@@ -37,18 +37,19 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-# Algorithmic ALU work per sample, in lane issue slots: the lean operation count of
+# Algorithmic ALU work per sample, in issue slots: the lean instruction count of
 # one sample -- Philox4x32-10 (10 rounds of two wide multiplies and two three-input
 # XORs per block), word-to-float conversions, radius and direction (hardware
 # sqrt / lg2+ex2 / sin / cos), index offsets, floor and fraction per axis, the
 # gather and multilinear interpolation, the two weight bands, and the sums (one
 # product and one pairwise addition per sum, and a four-operation compensated step
-# per block of B samples).  2D: 65.5 (a Philox block serves two samples; one
-# quad load of values and x-differences per bilinear gather; B = 8); 3D: 124.75
-# (three blocks per four samples; eight 8/16-bit taps, each one operation from
-# exact biased floats, four bases unbiased; B = 4).  The per-iteration reduction
-# and update are excluded.
-ALG_SLOTS_PER_SAMPLE = {2: 65.5, 3: 124.75}
+# per block of B samples), with each pair of independent FP32 operations that the
+# packed two-lane instructions can take counted as one slot.  2D: 52.75 (a Philox
+# block serves two samples; one quad load of row values and x-differences per
+# bilinear gather; B = 8); 3D: 102.25 (three blocks per four samples; eight
+# 8/16-bit taps, each one operation from exact biased floats; B = 4).  The
+# per-iteration reduction and update are excluded.
+ALG_SLOTS_PER_SAMPLE = {2: 52.75, 3: 102.25}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
 # ncu capture of the current kernel (to be removed when the kernel changes), scaled
 # with the volume and contour count: the 2048^2 instance of large-2d read 7.03 MB

@@ -105,11 +105,20 @@ __device__ __forceinline__ void fast_axis(float x, float M, int &idx, float &fr)
     fr = x - (t - M);
     idx = (int)__float_as_uint(t) - 0x4B000000;
 }
+// the same for the x and y axes in packed pairs
+__device__ __forceinline__ void fast_axes2(float2 x, float2 M, int &i0, int &i1, float2 &fr)
+{
+    const float2 t = __fadd2_rd(x, M);
+    fr = sub2(x, sub2(t, M));
+    i0 = (int)__float_as_uint(t.x) - 0x4B000000;
+    i1 = (int)__float_as_uint(t.y) - 0x4B000000;
+}
 
 // 2D region as quads: one shared-memory load feeds a bilinear sample.  With
-// `diff`, a quad holds (v00, v10 - v00, v01, v11 - v01), the x-differences the
-// interpolation needs (computed once per quad in FP32, as the sample would); else
-// (v00, v10, v01, v11).  Four halves (8 bytes) for uint8 voxels (values and
+// `diff`, a quad holds (v00, v01, v10 - v00, v11 - v01), the values of the two rows
+// and the x-differences the interpolation needs (computed once per quad in FP32, as
+// the sample would), so both rows are interpolated in one packed operation; else
+// (v00, v01, v10, v11).  Four halves (8 bytes) for uint8 voxels (values and
 // differences are integers below 2^9, exact in half precision) and binary16 voxels
 // (values only: their differences need not be representable), float4 otherwise.
 struct HQuad {
@@ -146,8 +155,10 @@ template <> __device__ __forceinline__ HQuad make_quad<HQuad>(float a, float b, 
 
 template <bool DIFF> __device__ __forceinline__ float quad_lerp(const float4 q, float f0, float f1)
 {
-    const float a0 = fmaf(f0, DIFF ? q.y : q.y - q.x, q.x), a1 = fmaf(f0, DIFF ? q.w : q.w - q.z, q.z);
-    return fmaf(f1, a1 - a0, a0);
+    const float2 v0 = make_float2(q.x, q.y);                       // (v00, v01)
+    const float2 d = DIFF ? make_float2(q.z, q.w) : sub2(make_float2(q.z, q.w), v0);
+    const float2 a = fma2(dup2(f0), d, v0);                        // the two rows at x
+    return fmaf(f1, a.y - a.x, a.x);
 }
 
 template <typename QT, bool DIFF> struct QuadFast {
@@ -159,10 +170,9 @@ template <typename QT, bool DIFF> struct QuadFast {
     __device__ __forceinline__ float at(float x0, float x1, float) const
     {
         int i0, i1;
-        float f0, f1;
-        fast_axis(x0, M[0], i0, f0);
-        fast_axis(x1, M[1], i1, f1);
-        return quad_lerp<DIFF>(quad_f(Q[checked(i1 * qp + i0, nq, st)]), f0, f1);
+        float2 fr;
+        fast_axes2(make_float2(x0, x1), make_float2(M[0], M[1]), i0, i1, fr);
+        return quad_lerp<DIFF>(quad_f(Q[checked(i1 * qp + i0, nq, st)]), fr.x, fr.y);
     }
 };
 
@@ -174,15 +184,21 @@ template <int DIM, typename T, typename LD>
 __device__ __forceinline__ float interp(const T *q, int64_t py, int64_t pz, float f0, float f1, float f2, LD ld)
 {
     constexpr float Z = LD::bias;
-    const float v00 = ld(q), v10 = ld(q + 1), v01 = ld(q + py), v11 = ld(q + py + 1);
-    const float a0 = fmaf(f0, v10 - v00, v00 - Z), a1 = fmaf(f0, v11 - v01, v01 - Z);
-    const float s0 = fmaf(f1, a1 - a0, a0);
-    if (DIM == 2) return s0;
+    if (DIM == 2) {
+        const float2 lo = make_float2(ld(q), ld(q + py)), hi = make_float2(ld(q + 1), ld(q + py + 1));
+        const float2 base = Z != 0.0f ? sub2(lo, dup2(Z)) : lo;
+        const float2 a = fma2(dup2(f0), sub2(hi, lo), base);      // (row y0, row y1) at x
+        return fmaf(f1, a.y - a.x, a.x);
+    }
+    // x-interpolation of rows (y0, z0) and (y0, z1) as one pair, (y1, z0) and
+    // (y1, z1) as the other; then y for both planes at once, then z
     const T *r = q + pz;
-    const float w00 = ld(r), w10 = ld(r + 1), w01 = ld(r + py), w11 = ld(r + py + 1);
-    const float b0 = fmaf(f0, w10 - w00, w00 - Z), b1 = fmaf(f0, w11 - w01, w01 - Z);
-    const float s1 = fmaf(f1, b1 - b0, b0);
-    return fmaf(f2, s1 - s0, s0);
+    const float2 lo0 = make_float2(ld(q), ld(r)), hi0 = make_float2(ld(q + 1), ld(r + 1));
+    const float2 lo1 = make_float2(ld(q + py), ld(r + py)), hi1 = make_float2(ld(q + py + 1), ld(r + py + 1));
+    const float2 a0 = fma2(dup2(f0), sub2(hi0, lo0), Z != 0.0f ? sub2(lo0, dup2(Z)) : lo0);
+    const float2 a1 = fma2(dup2(f0), sub2(hi1, lo1), Z != 0.0f ? sub2(lo1, dup2(Z)) : lo1);
+    const float2 sz = fma2(dup2(f1), sub2(a1, a0), a0);           // (plane z0, plane z1)
+    return fmaf(f2, sz.y - sz.x, sz.x);
 }
 
 // Tap loaders (biased taps for integer voxels, see interp); base, n and st serve
@@ -225,11 +241,11 @@ template <int DIM, typename T> struct RawFast {
     __device__ __forceinline__ float at(float x0, float x1, float x2) const
     {
         int i0, i1, i2 = 0;
-        float f0, f1, f2 = 0.0f;
-        fast_axis(x0, M[0], i0, f0);
-        fast_axis(x1, M[1], i1, f1);
+        float2 fr;
+        float f2 = 0.0f;
+        fast_axes2(make_float2(x0, x1), make_float2(M[0], M[1]), i0, i1, fr);
         if (DIM == 3) fast_axis(x2, M[2], i2, f2);
-        return interp<DIM, T>(p + i0 + i1 * py + i2 * pz, py, pz, f0, f1, f2, SmemLoad<T>{p, n, st});
+        return interp<DIM, T>(p + i0 + i1 * py + i2 * pz, py, pz, fr.x, fr.y, f2, SmemLoad<T>{p, n, st});
     }
 };
 
@@ -283,69 +299,73 @@ template <int DIM, typename T> struct GlobalClamp {
 // of the five sums J = sum S I, J_R = sum dS/dR I, J_c = sum -S'(r) (raw
 // direction) I for one sample.
 struct Terms {
-    float v[5];
+    float2 a;   // (S I, dS/dR I)
+    float2 b;   // -S' I times raw direction (d0, d1)
+    float c;    // -S' I d2 (3D)
 };
 
 template <int DIM>
 __device__ __forceinline__ Terms sample_terms(const IterC<DIM> &ic, const EvolveArgs &a, float rv, float I, float d0,
                                               float d1, float d2)
 {
-    const float t1 = fmaf(rv, ic.A1, ic.B1), t2 = fmaf(rv, ic.A2, ic.B2);
-    const float r1 = __saturatef(t1), r2 = __saturatef(t2);
+    const float2 t = fma2(dup2(rv), make_float2(ic.A1, ic.A2), make_float2(ic.B1, ic.B2));   // band coordinates
+    const float r1 = __saturatef(t.x), r2 = __saturatef(t.y);
     const float S = fmaf(2.0f, r1, -1.0f) - r2;
     // I where the sample lies inside the inner / outer band (slopes there), else 0
-    const float m1 = r1 == t1 ? I : 0.0f, m2 = r2 == t2 ? I : 0.0f;
-    const float g = fmaf(a.kr1, m1, a.kr2 * m2);
-    Terms t;
-    t.v[0] = S * I;
-    t.v[1] = fmaf(a.kR1, m1, a.kR2 * m2);
-    t.v[2] = g * d0;
-    t.v[3] = g * d1;
-    t.v[4] = DIM == 3 ? g * d2 : 0.0f;
-    return t;
+    const float m1 = r1 == t.x ? I : 0.0f, m2 = r2 == t.y ? I : 0.0f;
+    // (-S' I, dS/dR I) = (kr1, kR1) m1 + (kr2, kR2) m2
+    const float2 gk = fma2(make_float2(a.kr1, a.kR1), dup2(m1), mul2(make_float2(a.kr2, a.kR2), dup2(m2)));
+    Terms o;
+    o.a = make_float2(S * I, gk.y);
+    o.b = mul2(dup2(gk.x), make_float2(d0, d1));
+    o.c = DIM == 3 ? gk.x * d2 : 0.0f;
+    return o;
 }
 
-// Adds the terms of one or two samples: the pair is summed in one rounding, then
-// added with Kahan compensation (COMP) or plainly.
-template <int DIM, bool COMP>
-__device__ __forceinline__ void add_terms(KSum *acc, const Terms &x)
-{
-#pragma unroll
-    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) {
-        if (COMP) kadd(acc[i], x.v[i]);
-        else acc[i].s += x.v[i];
-    }
-}
-template <int DIM, bool COMP>
-__device__ __forceinline__ void add_terms(KSum *acc, const Terms &x, const Terms &y)
-{
-#pragma unroll
-    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) {
-        if (COMP) kadd(acc[i], x.v[i] + y.v[i]);
-        else acc[i].s += x.v[i] + y.v[i];
-    }
-}
+// Per-lane accumulators of the five sums: (J, J_R) and (J_c0, J_c1) as packed
+// pairs, J_c2 alone.
+struct Acc {
+    KSum2 a, b;
+    KSum c;
+};
 
-// Four samples (two Philox blocks in 2D) summed pairwise in two roundings, then
-// one compensated addition: fewer additions per sample than pair-wise steps.
-template <int DIM, bool COMP>
-__device__ __forceinline__ void add_terms4(KSum *acc, const Terms &x, const Terms &y, const Terms &z, const Terms &w)
+// Adds the terms of one sample, or the sum of two in one rounding, with Kahan
+// compensation (COMP) or plainly.
+template <int DIM, bool COMP> __device__ __forceinline__ void add_terms(Acc &acc, const Terms &x)
 {
-#pragma unroll
-    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) {
-        const float s = (x.v[i] + y.v[i]) + (z.v[i] + w.v[i]);
-        if (COMP) kadd(acc[i], s);
-        else acc[i].s += s;
+    if (COMP) {
+        kadd2(acc.a, x.a);
+        kadd2(acc.b, x.b);
+        if (DIM == 3) kadd(acc.c, x.c);
+    } else {
+        acc.a.s = add2(acc.a.s, x.a);
+        acc.b.s = add2(acc.b.s, x.b);
+        if (DIM == 3) acc.c.s += x.c;
     }
 }
-
-// Pairwise sum of four samples, kept to be joined with the next four.
-template <int DIM> __device__ __forceinline__ Terms sum4(const Terms &x, const Terms &y, const Terms &z, const Terms &w)
+template <int DIM> __device__ __forceinline__ Terms sum2(const Terms &x, const Terms &y)
 {
     Terms h;
-#pragma unroll
-    for (int i = 0; i < (DIM == 3 ? 5 : 4); ++i) h.v[i] = (x.v[i] + y.v[i]) + (z.v[i] + w.v[i]);
+    h.a = add2(x.a, y.a);
+    h.b = add2(x.b, y.b);
+    h.c = DIM == 3 ? x.c + y.c : 0.0f;
     return h;
+}
+template <int DIM, bool COMP> __device__ __forceinline__ void add_terms(Acc &acc, const Terms &x, const Terms &y)
+{
+    add_terms<DIM, COMP>(acc, sum2<DIM>(x, y));
+}
+
+// Pairwise sum of four samples in two roundings (kept to be joined with the next
+// four, or added with one compensated step: fewer additions per sample).
+template <int DIM> __device__ __forceinline__ Terms sum4(const Terms &x, const Terms &y, const Terms &z, const Terms &w)
+{
+    return sum2<DIM>(sum2<DIM>(x, y), sum2<DIM>(z, w));
+}
+template <int DIM, bool COMP>
+__device__ __forceinline__ void add_terms4(Acc &acc, const Terms &x, const Terms &y, const Terms &z, const Terms &w)
+{
+    add_terms<DIM, COMP>(acc, sum4<DIM>(x, y, z, w));
 }
 
 // All samples of one contour-iteration handled by this lane (lane `lig` of G).
@@ -375,18 +395,17 @@ template <int DIM, bool ACC, typename Gather>
 __device__ __forceinline__ Terms sample3(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a, uint32_t w0,
                                          uint32_t w1, uint32_t w2)
 {
-    const float u0 = top24(w0) * 5.9604644775390625e-8f;
+    const float2 ut = mul2(make_float2(top24(w0), top24(w1)), dup2(5.9604644775390625e-8f));
+    const float u0 = ut.x, t = ut.y;
     const float rv = ACC ? cbrtf(u0) : ex2_approx(lg2_approx(u0) * (1.0f / 3.0f));
-    const float t = top24(w1) * 5.9604644775390625e-8f;
     const float cphi = fmaf(-2.0f, t, 1.0f);
     const float sh = ACC ? sqrtf(t * (1.0f - t)) : sqrt_approx(t * (1.0f - t));
     float c0, s0;
     raw_direction2<DIM, ACC>(w2, c0, s0);
-    const float d0 = sh * c0, d1 = sh * s0;
-    const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
-    const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
+    const float2 d = mul2(dup2(sh), make_float2(c0, s0));
+    const float2 x = fma2(mul2(dup2(rv), make_float2(ic.K[0], ic.K[1])), d, make_float2(ic.ax[0].cf, ic.ax[1].cf));
     const float x2 = fmaf(rv * ic.K[2], cphi, ic.ax[2].cf);
-    return sample_terms<DIM>(ic, a, rv, gat.at(x0, x1, x2), d0, d1, cphi);
+    return sample_terms<DIM>(ic, a, rv, gat.at(x.x, x.y, x2), d.x, d.y, cphi);
 }
 
 template <int DIM, bool ACC, typename Gather>
@@ -396,14 +415,14 @@ __device__ __forceinline__ Terms sample2(const Gather &gat, const IterC<DIM> &ic
     const float rv = ACC ? sqrtf(top24(wr)) : sqrt_approx(top24(wr));
     float d0, d1;
     raw_direction2<DIM, ACC>(wa, d0, d1);
-    const float x0 = fmaf(rv * ic.K[0], d0, ic.ax[0].cf);
-    const float x1 = fmaf(rv * ic.K[1], d1, ic.ax[1].cf);
-    return sample_terms<DIM>(ic, a, rv, gat.at(x0, x1, 0.0f), d0, d1, 0.0f);
+    const float2 x = fma2(mul2(dup2(rv), make_float2(ic.K[0], ic.K[1])), make_float2(d0, d1),
+                          make_float2(ic.ax[0].cf, ic.ax[1].cf));
+    return sample_terms<DIM>(ic, a, rv, gat.at(x.x, x.y, 0.0f), d0, d1, 0.0f);
 }
 
 template <int DIM, int G, bool COMP, bool ACC, typename Gather>
 __device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a,
-                                               uint32_t n, uint32_t k, uint32_t stream, int lig, KSum *acc)
+                                               uint32_t n, uint32_t k, uint32_t stream, int lig, Acc &acc)
 {
     if constexpr (DIM == 3) {
         // a lane takes quads q, q + G, ...: three Philox blocks give its four
@@ -585,11 +604,15 @@ template <int DIM, int G, bool COMP, bool ACC, typename Gather>
 __device__ __forceinline__ Step eval_contour(const Gather &gat, const IterC<DIM> &ic, float R, const EvolveArgs &a,
                                              int n, uint32_t k, uint32_t stream, float scale, int lig, unsigned mask)
 {
-    KSum acc[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    Acc acc;
+    acc.a.s = acc.a.c = acc.b.s = acc.b.c = make_float2(0.0f, 0.0f);
+    acc.c.s = acc.c.c = 0.0f;
     sample_contour<DIM, G, COMP, ACC>(gat, ic, a, (uint32_t)n, k, stream, lig, acc);
+    const KSum k5[5] = {{acc.a.s.x, acc.a.c.x}, {acc.a.s.y, acc.a.c.y}, {acc.b.s.x, acc.b.c.x},
+                        {acc.b.s.y, acc.b.c.y}, {acc.c.s, acc.c.c}};
     float sums[5];
     sums[4] = 0.0f;
-    group_reduce_all<G, COMP, DIM == 3 ? 5 : 4>(acc, sums, mask);
+    group_reduce_all<G, COMP, DIM == 3 ? 5 : 4>(k5, sums, mask);
     return finish<DIM>(sums, R, a, scale);
 }
 
@@ -667,7 +690,7 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
             const T *r = reg + y * a.ext[0] + x;
             const float v00 = to_f<T>(r[0]), v10 = to_f<T>(r[1]);
             const float v01 = to_f<T>(r[a.ext[0]]), v11 = to_f<T>(r[a.ext[0] + 1]);
-            Q[i] = QuadOf<T>::diff ? make_quad<QT>(v00, v10 - v00, v01, v11 - v01) : make_quad<QT>(v00, v10, v01, v11);
+            Q[i] = QuadOf<T>::diff ? make_quad<QT>(v00, v01, v10 - v00, v11 - v01) : make_quad<QT>(v00, v01, v10, v11);
         }
         __syncthreads();
     }

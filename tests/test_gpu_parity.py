@@ -210,6 +210,20 @@ def test_teacher_forced_storage_types(ac, oracle, brain_small, kind):
     assert frac >= 0.9999, (frac, nflag, worst, bad)
 
 
+@pytest.mark.parametrize("N,G", [(115, 4), (112, 4), (100, 4), (31, 8), (9, 16), (130, 16)])
+def test_teacher_forced_2d_ragged(ac, oracle, crop2d, N, G):
+    """2D sample counts that exercise every part of a lane's loop: groups of four
+    Philox blocks, a pair of blocks, a leftover block and an odd N's last sample
+    (N = 115 at 4 lanes: 15 blocks on lane 0, 14 on the others, one lone sample)."""
+    s = crop2d
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(2, R0, s.contrast, N=N, T=12, seed=17, lanes_per_contour=G)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(1000, 1800))
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 1000, 1)
+    assert frac >= 0.9999, (frac, nflag, worst, bad)
+
+
 # ------------------------------------------------------------------ edge cases
 @pytest.mark.parametrize("N,T,G,sampling", [(1, 3, 32, 0), (2, 3, 8, 0), (33, 4, 32, 0), (100, 5, 16, 0),
                                             (7, 2, 8, 0), (256, 3, 16, 1), (100, 3, 32, 2)])
