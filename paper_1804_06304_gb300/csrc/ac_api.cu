@@ -398,7 +398,7 @@ namespace {
 struct Plan {
     int B[3], halo[3], ext[3];
     int raw;        // staged region bytes
-    int quad_off;   // 2D: byte offset of the float4 quads (0: none)
+    int quad_off;   // 2D: byte offset of the quads (0: none)
     int smem;       // dynamic shared memory bytes
     int G, warps;
     bool brick, grid, comp, acc;

@@ -636,7 +636,7 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *keys, int64_t
 
 // ----------------------------------------------------------------- brick kernel
 // One CTA per brick: TMA stages the brick plus halo into shared memory once (2D:
-// then rewritten as float4 quads so one 128-bit load feeds a bilinear sample);
+// then rewritten as quads so one shared-memory load feeds a bilinear sample);
 // each group of G lanes evolves one contour of the brick through all iterations
 // with its state in registers ("Parallel Contour Evaluation": lanes share the
 // samples of a contour).  Per iteration a group takes the fast path (ball inside
