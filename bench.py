@@ -160,16 +160,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------ oracle leg
-def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0, threads: int = 0):
+def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0, threads: int = 0, seed: int = 7,
+                  states: bool = False):
     """Time the FP64 oracle (all host cores, or `threads`) on a random subset of the
-    workload's contours, sized to take about `seconds`; returns (samples/s, threads,
-    sample text)."""
+    workload's contours, sized to take about `seconds`, with Philox key `seed`;
+    returns (samples/s, threads, sample text), and with ``states`` also the contour
+    indices of the subset and the oracle's final cR (m x 4) and E (m,)."""
     from oracle import oracle
     ndim = wl["ndim"]
     seeds = oracle.seed_lattice(ndim, s.shape_xyz, spacing, wl["stride"])
     R0 = seeds[0, 3]
     op = oracle.make_params(ndim, wl["N"], wl["T"], eps0=8 * R0 * R0 / s.contrast, dR=1.0,
-                            Rmin=max(0.5, 0.5 * R0), Rmax=3 * R0, max_step=0.5, seed=7)
+                            Rmin=max(0.5, 0.5 * R0), Rmax=3 * R0, max_step=0.5, seed=seed)
     img = oracle.VolumeImage(vol, spacing)
     threads = threads or oracle.max_threads()
     rng = np.random.default_rng(rng_seed)
@@ -182,10 +184,40 @@ def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0, thread
     m = int(min(len(seeds), max(pilot, seconds / max(per, 1e-9))))
     idx = rng.choice(len(seeds), m, replace=False)
     t0 = time.perf_counter()
-    oracle.evolve(img, op, seeds[idx], ids=idx, nthreads=threads)
+    cR, E, _ = oracle.evolve(img, op, seeds[idx], ids=idx, nthreads=threads)
     dt = time.perf_counter() - t0
     samples = m * wl["N"] * wl["T"]
-    return samples / dt, threads, f"{m} of {len(seeds)} contours (random, seed {rng_seed}), all {wl['T']} iterations"
+    desc = f"{m} of {len(seeds)} contours (random, seed {rng_seed}), all {wl['T']} iterations"
+    if states:
+        return samples / dt, threads, desc, idx, cR, E
+    return samples / dt, threads, desc
+
+
+def oracle_check(gpu_state: np.ndarray, idx: np.ndarray, cR: np.ndarray, E: np.ndarray, spacing, ndim: int,
+                 E0: float = 0.0) -> dict:
+    """Final states of the FP32 GPU run against the FP64 oracle's, free-running from
+    the same seeds and Philox streams, on the oracle's contour subset: centre error
+    in voxels (the 0.25-voxel bar of the free-running parity tests), over all
+    contours and over the converged ones (oracle energy below E0), radius and
+    energy errors."""
+    g = gpu_state[:, idx].astype(np.float64)
+    sp = np.asarray(spacing[:ndim], np.float64)
+    dc = np.linalg.norm((g[:ndim].T - cR[:, :ndim]) / sp, axis=1)
+    dR = np.abs(g[3] - cR[:, 3])
+    dE = np.abs(g[4] - E)
+    return {"contours": int(len(idx)), "centre_err_voxels": {"median": float(np.median(dc)),
+                                                             "p99": float(np.quantile(dc, 0.99)),
+                                                             "max": float(dc.max())},
+            "frac_centre_within_0.25_voxel": float(np.mean(dc <= 0.25)),
+            "converged": {"contours": int(np.sum(E < E0)),
+                          "frac_centre_within_0.25_voxel": float(np.mean(dc[E < E0] <= 0.25)) if np.any(E < E0)
+                          else None},
+            "radius_err_max": float(dR.max()),
+            "energy_abs_err_median": float(np.median(dE)), "energy_abs_median": float(np.median(np.abs(E))),
+            "note": "free-running final states after all iterations from the same seeds and Philox "
+                    "streams: a last-bit FP32 difference can send a contour near a saddle between "
+                    "touching nuclei, or on background noise, to another end point; per-iteration "
+                    "agreement is the teacher-forced parity of the tests"}
 
 
 def oracle_sample_batch(vols, wl, seconds: float, rng_seed: int = 0):
@@ -347,6 +379,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     launches = ac.ac_kernel_launches() - launches0
     paths = ac.ac_evolve_stats(C)
+    final_state = ac.ac_get_state(C) if rank == 0 and not args.no_cpu_baseline else None
     if dist_on:
         dist.barrier()
     torch.cuda.synchronize()
@@ -432,10 +465,13 @@ def main(argv=None):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.path != "grid":
-        v, thr, desc = oracle_sample(s, vol, wl, spacing, args.cpu_seconds)
+        v, thr, desc, idx, o_cR, o_E = oracle_sample(s, vol, wl, spacing, args.cpu_seconds, seed=params.seed,
+                                                     states=True)
         v1, _, desc1 = oracle_sample(s, vol, wl, spacing, min(3.0, args.cpu_seconds), rng_seed=1, threads=1)
         cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc,
                "one_thread": {"value": v1, "sample": desc1}}
+        if not rules:
+            cpu["oracle_check"] = oracle_check(final_state, idx, o_cR, o_E, spacing, ndim, E0)
     citers = C.count * wl["T"]
 
     if rank == 0 and args.path == "grid":

@@ -65,3 +65,28 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_oracle_check_measures_centre_error_in_voxels():
+    """The bench's oracle check: identical states give zero error; a centre shifted
+    by 0.5 physical units along an axis of spacing 2 is 0.25 voxel off."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(3)
+    C = 50
+    state = rng.uniform(1, 20, size=(5, C)).astype(np.float32)
+    idx = np.array([3, 7, 11, 40])
+    cR = state[:4, idx].T.astype(np.float64)
+    E = state[4, idx].astype(np.float64)
+    ok = bench.oracle_check(state, idx, cR, E, (1.0, 1.0, 2.0), 3)
+    assert ok["contours"] == 4 and ok["centre_err_voxels"]["max"] == 0.0
+    assert ok["frac_centre_within_0.25_voxel"] == 1.0 and ok["radius_err_max"] == 0.0
+    moved = state.copy()
+    moved[2, 11] += 0.5
+    moved[0, 40] += 0.6
+    chk = bench.oracle_check(moved, idx, cR, E, (1.0, 1.0, 2.0), 3)
+    assert abs(chk["centre_err_voxels"]["max"] - 0.6) < 1e-5
+    assert chk["frac_centre_within_0.25_voxel"] == 0.75      # 0.25 voxel passes, 0.6 does not
+    conv = bench.oracle_check(moved, idx, cR, E, (1.0, 1.0, 2.0), 3, E0=float(np.sort(E)[2]))
+    assert conv["converged"]["contours"] == 2
