@@ -204,7 +204,6 @@ extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const
     if (!out) AC_FAIL(AC_ERR_ARG, "ac_seed: out is NULL");
     *out = nullptr;
     if (!vol) AC_FAIL(AC_ERR_ARG, "ac_seed: vol is NULL");
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     if (n_explicit < 0) AC_FAIL(AC_ERR_ARG, "ac_seed: n_explicit is negative");
     if (explicit_cR && n_explicit == 0) {   // an empty set
         ac_contours *c = nullptr;
