@@ -112,9 +112,10 @@ ac_status ac_server_submit(ac_server *srv, const void *data_host, const int64_t 
  * tile to finish.  When it has: copies up to `cap` cells (acceptance order, as
  * ac_localize) to `cells_out`, fills *result, releases the ticket and returns the
  * tile's own status (AC_OK, or the error that ended it, with its message).  When
- * it has not: returns AC_ERR_TIMEOUT and the ticket stays valid.  Errors:
- * AC_ERR_ARG (unknown or collected ticket, null result), AC_ERR_TIMEOUT, and the
- * tile's errors (AC_ERR_CUDA, AC_ERR_OOM, AC_ERR_NUMERIC, ...).
+ * it has not: returns AC_ERR_TIMEOUT and the ticket stays valid.  Several threads may
+ * wait on one ticket: the first to wake collects it, the others return AC_ERR_ARG.
+ * Errors: AC_ERR_ARG (unknown or collected ticket, null result), AC_ERR_TIMEOUT, and
+ * the tile's errors (AC_ERR_CUDA, AC_ERR_OOM, AC_ERR_NUMERIC, ...).
  */
 ac_status ac_server_wait(ac_server *srv, int64_t ticket, double timeout_s, ac_cell *cells_out, int64_t cap,
                          ac_tile_result *result);

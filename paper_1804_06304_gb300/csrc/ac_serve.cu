@@ -335,13 +335,19 @@ extern "C" ac_status ac_server_wait(ac_server *S, int64_t ticket, double timeout
     if (!S || !result) AC_FAIL(AC_ERR_ARG, "ac_server_wait: NULL argument");
     if (cap > 0 && !cells_out) AC_FAIL(AC_ERR_ARG, "ac_server_wait: cells_out is NULL");
     std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->tiles.find(ticket);
-    if (it == S->tiles.end()) AC_FAIL(AC_ERR_ARG, "ac_server_wait: unknown or collected ticket");
-    Tile *t = it->second;
-    auto ready = [&] { return t->done; };
+    if (S->tiles.find(ticket) == S->tiles.end()) AC_FAIL(AC_ERR_ARG, "ac_server_wait: unknown or collected ticket");
+    // another thread may collect the ticket while this one waits: look it up again
+    // on every wake-up instead of keeping a pointer to the tile
+    auto ready = [&] {
+        const auto f = S->tiles.find(ticket);
+        return f == S->tiles.end() || f->second->done;
+    };
     if (timeout_s < 0) S->cv_done.wait(lk, ready);
     else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready))
         AC_FAIL(AC_ERR_TIMEOUT, "ac_server_wait: tile not finished yet");
+    const auto it = S->tiles.find(ticket);
+    if (it == S->tiles.end()) AC_FAIL(AC_ERR_ARG, "ac_server_wait: ticket collected by another caller");
+    Tile *t = it->second;
     std::memset(result, 0, sizeof(*result));
     result->ticket = t->ticket;
     result->status = t->status;
