@@ -8,8 +8,9 @@ compensated warp reductions, gradient steps) and localize (a9: energy cull and
 overlap competition, cells copied to the host).
 
 Metric: MC contour samples per second (contours x samples x iterations per step /
-step time), the default workload being the 4096x4096 2D image with ~12k nuclei
-(stride-6 lattice, 128 samples, 100 iterations).  `value` is measured with the
+step time), the default workload being the 1024x1024x256 uint16 brain-like volume
+with ~100k nuclei (spacing 1:1:2, stride-6 lattice of 2,456,500 contours, 512
+samples, 100 iterations); `--workload large-2d` runs the 4096x4096 2D image.  `value` is measured with the
 input already in HBM; `e2e` repeats the step through the same C ABI from pinned
 host memory (host-to-device copy of the image and device-to-host copy of the cells
 inside the timed region).  The roofline entry covers the evolution kernel (plain
@@ -193,31 +194,129 @@ def oracle_sample(s, vol, wl, spacing, seconds: float, rng_seed: int = 0, thread
     return samples / dt, threads, desc
 
 
+def oracle_params_of(oracle, ndim: int, p):
+    """The oracle's parameters for the library's evolve parameters ``p``, every real
+    rounded to FP32 as the library receives it, so that both sides start from the
+    same numbers."""
+    f = lambda x: float(np.float32(x))  # noqa: E731
+    return oracle.make_params(ndim, p.N, p.T, eps0=f(p.eps0), dR=f(p.dR), Rmin=f(p.Rmin), Rmax=f(p.Rmax),
+                              max_step=f(p.max_step), seed=p.seed, stream_id=p.stream_id)
+
+
+def lattice_shape(shape_xyz, spacing, stride, ndim):
+    return [max(1, int(math.floor(shape_xyz[d] * spacing[d] / stride))) for d in range(ndim)]
+
+
+def window_ids(L, m: int) -> np.ndarray:
+    """Contour indices (x fastest, as the lattice numbers them) of a centred box of
+    about ``m`` lattice cells."""
+    ndim = len(L)
+    side = max(1, int(round(m ** (1.0 / ndim))))
+    ranges = []
+    for d in range(ndim):
+        w = min(L[d], side)
+        lo = (L[d] - w) // 2
+        ranges.append(np.arange(lo, lo + w, dtype=np.int64))
+    k = np.zeros([len(r) for r in ranges], np.int64)
+    mul = 1
+    for d in range(ndim):
+        shape = [1] * ndim
+        shape[d] = len(ranges[d])
+        k = k + ranges[d].reshape(shape) * mul
+        mul *= L[d]
+    return np.sort(k.ravel())
+
+
+def oracle_window(s, vol, wl, spacing, init_state, p, seconds: float, threads: int = 0):
+    """The FP64 oracle on every contour of a centred window of the lattice, sized to
+    take about ``seconds`` on ``threads`` host threads (all by default), started from
+    the GPU run's own initial FP32 state with its FP32 parameters and Philox key.
+    Returns (samples/s, threads, sample text, window ids, final cR (m x 4), E (m,))."""
+    from oracle import oracle
+    ndim = wl["ndim"]
+    L = lattice_shape(s.shape_xyz, spacing, wl["stride"], ndim)
+    op = oracle_params_of(oracle, ndim, p)
+    img = oracle.VolumeImage(vol, tuple(float(np.float32(v)) for v in spacing))
+    threads = threads or oracle.max_threads()
+    seeds = init_state[:4].T.astype(np.float64)
+    pilot = window_ids(L, max(threads * 8, 64))
+    t0 = time.perf_counter()
+    oracle.evolve(img, op, seeds[pilot], ids=pilot, nthreads=threads)
+    per = (time.perf_counter() - t0) / len(pilot)
+    ids = window_ids(L, int(max(len(pilot), seconds / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    cR, E, _ = oracle.evolve(img, op, seeds[ids], ids=ids, nthreads=threads)
+    dt = time.perf_counter() - t0
+    box = "x".join(str(len(np.unique((ids // int(np.prod(L[:d]))) % L[d]))) for d in range(ndim))
+    desc = (f"every contour of a centred {box} window of the {'x'.join(map(str, L))} lattice ({len(ids)} of "
+            f"{int(np.prod(L))}), all {wl['T']} iterations")
+    return len(ids) * wl["N"] * wl["T"] / dt, threads, desc, ids, cR, E
+
+
+def match_points(a: np.ndarray, b: np.ndarray, tol: float) -> int:
+    """One-to-one greedy matching of two point sets within ``tol``, closest pairs
+    first; returns the number of matched pairs."""
+    if len(a) == 0 or len(b) == 0:
+        return 0
+    from scipy.spatial import cKDTree
+    pairs = cKDTree(a).query_ball_tree(cKDTree(b), tol)
+    cand = [(float(np.linalg.norm(a[i] - b[j])), i, j) for i, js in enumerate(pairs) for j in js]
+    cand.sort()
+    ua, ub, m = set(), set(), 0
+    for _, i, j in cand:
+        if i not in ua and j not in ub:
+            ua.add(i)
+            ub.add(j)
+            m += 1
+    return m
+
+
+def window_cells(ac, V, gpu_state: np.ndarray, idx: np.ndarray, E0: float) -> np.ndarray:
+    """The library's localization (ac_localize) of the window's contours alone, with
+    the GPU run's final states: the cells the oracle's localization is compared with."""
+    sub = ac.ac_seed(V, explicit=np.ascontiguousarray(gpu_state[:4, idx].T))
+    ac.ac_set_state(sub, np.ascontiguousarray(gpu_state[:, idx]))
+    return ac.ac_localize(sub, float(np.float32(E0)))
+
+
 def oracle_check(gpu_state: np.ndarray, idx: np.ndarray, cR: np.ndarray, E: np.ndarray, spacing, ndim: int,
-                 E0: float = 0.0) -> dict:
-    """Final states of the FP32 GPU run against the FP64 oracle's, free-running from
-    the same seeds and Philox streams, on the oracle's contour subset: centre error
-    in voxels (the 0.25-voxel bar of the free-running parity tests), over all
-    contours and over the converged ones (oracle energy below E0), radius and
-    energy errors."""
+                 E0: float = 0.0, gpu_cells=None) -> dict:
+    """Final states of the FP32 GPU run against the FP64 oracle's on the oracle's
+    contours, both free-running from the same FP32 seeds, parameters and Philox
+    streams: centre error in voxels (the 0.25-voxel bar), over all contours and over
+    the converged ones (oracle energy below E0), radius and energy errors; with
+    ``gpu_cells`` (the library's localization of the same contours, centres in
+    physical units) also the detection-set agreement 2 |matched| / (|D_gpu| +
+    |D_oracle|) against the oracle's own overlap competition (one-to-one matches
+    within 0.5 voxel)."""
     g = gpu_state[:, idx].astype(np.float64)
     sp = np.asarray(spacing[:ndim], np.float64)
     dc = np.linalg.norm((g[:ndim].T - cR[:, :ndim]) / sp, axis=1)
     dR = np.abs(g[3] - cR[:, 3])
     dE = np.abs(g[4] - E)
-    return {"contours": int(len(idx)), "centre_err_voxels": {"median": float(np.median(dc)),
-                                                             "p99": float(np.quantile(dc, 0.99)),
-                                                             "max": float(dc.max())},
-            "frac_centre_within_0.25_voxel": float(np.mean(dc <= 0.25)),
-            "converged": {"contours": int(np.sum(E < E0)),
-                          "frac_centre_within_0.25_voxel": float(np.mean(dc[E < E0] <= 0.25)) if np.any(E < E0)
-                          else None},
-            "radius_err_max": float(dR.max()),
-            "energy_abs_err_median": float(np.median(dE)), "energy_abs_median": float(np.median(np.abs(E))),
-            "note": "free-running final states after all iterations from the same seeds and Philox "
-                    "streams: a last-bit FP32 difference can send a contour near a saddle between "
-                    "touching nuclei, or on background noise, to another end point; per-iteration "
-                    "agreement is the teacher-forced parity of the tests"}
+    conv = E < E0
+    out = {"contours": int(len(idx)), "centre_err_voxels": {"median": float(np.median(dc)),
+                                                            "p99": float(np.quantile(dc, 0.99)),
+                                                            "max": float(dc.max())},
+           "frac_centre_within_0.25_voxel": float(np.mean(dc <= 0.25)),
+           "converged": {"contours": int(np.sum(conv)),
+                         "frac_centre_within_0.25_voxel": float(np.mean(dc[conv] <= 0.25)) if np.any(conv)
+                         else None},
+           "radius_err_max": float(dR.max()),
+           "energy_abs_err_median": float(np.median(dE)), "energy_abs_median": float(np.median(np.abs(E))),
+           "note": "free-running final states after all iterations from the same FP32 seeds, FP32 "
+                   "parameters and Philox streams; a last-bit difference can send a contour near a saddle "
+                   "between touching nuclei, or on background noise, to another end point; per-iteration "
+                   "agreement is the teacher-forced parity of the tests"}
+    if gpu_cells is not None:
+        from oracle import oracle
+        ids_o = oracle.localize(ndim, cR, E, float(np.float32(E0)))
+        dg = np.asarray(gpu_cells, np.float64).reshape(-1, 3)[:, :ndim] / sp
+        do = cR[ids_o, :ndim] / sp
+        m = match_points(dg, do, 0.5)
+        out["detections"] = {"gpu": int(len(dg)), "oracle": int(len(do)), "matched": int(m),
+                             "agreement": 2.0 * m / max(len(dg) + len(do), 1)}
+    return out
 
 
 def oracle_sample_batch(vols, wl, seconds: float, rng_seed: int = 0):
@@ -263,6 +362,15 @@ def torch_max_reducer(device):
     return f
 
 
+def image_config(args, wl, contours: int, world: int) -> dict:
+    """The ``config`` of a single-image workload, identical in both arms."""
+    rules = {k: v for k, v in (("freeze", args.freeze), ("cull", args.cull)) if v}
+    return {"workload": args.workload + (f"@{args.size}" if args.size else ""), "desc": wl["desc"],
+            "contours": int(contours), "samples": wl["N"], "iterations": wl["T"], "path": args.path,
+            "dtype": args.dtype, "stopping_rules": rules or None,
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"}
+
+
 # ------------------------------------------------------------------------ main
 def main(argv=None):
     ap = argparse.ArgumentParser()
@@ -270,7 +378,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large-2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="brain-3d", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default="native", choices=["native", "f16"])
     ap.add_argument("--path", default="brick", choices=["brick", "plain", "grid"],
                     help="grid: the voxel-grid form of Eq. 5 instead of Monte-Carlo samples")
@@ -324,6 +432,7 @@ def main(argv=None):
     V = ac.ac_create_volume(vol_dev, spacing, dtype=dcode)
     C = ac.ac_seed(V, stride=wl["stride"])
     assert C.count == C_expected, (C.count, C_expected)
+    init_state = ac.ac_get_state(C)    # the lattice every step re-seeds (the oracle check starts from it)
     R0 = wl["stride"] / math.sqrt(1.5)
     params = ac.default_params(ndim, R0, s.contrast, N=wl["N"], T=wl["T"], seed=1000 + rank,
                                path={"brick": ac.AC_PATH_BRICK, "plain": ac.AC_PATH_PLAIN,
@@ -465,13 +574,13 @@ def main(argv=None):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.path != "grid":
-        v, thr, desc, idx, o_cR, o_E = oracle_sample(s, vol, wl, spacing, args.cpu_seconds, seed=params.seed,
-                                                     states=True)
+        v, thr, desc, idx, o_cR, o_E = oracle_window(s, vol, wl, spacing, init_state, params, args.cpu_seconds)
         v1, _, desc1 = oracle_sample(s, vol, wl, spacing, min(3.0, args.cpu_seconds), rng_seed=1, threads=1)
         cpu = {"value": v, "unit": "samples/s", "cores": thr, "kind": "oracle", "sample": desc,
                "one_thread": {"value": v1, "sample": desc1}}
         if not rules:
-            cpu["oracle_check"] = oracle_check(final_state, idx, o_cR, o_E, spacing, ndim, E0)
+            cells_w = window_cells(ac, V, final_state, idx, E0)
+            cpu["oracle_check"] = oracle_check(final_state, idx, o_cR, o_E, spacing, ndim, E0, cells_w["c"])
     citers = C.count * wl["T"]
 
     if rank == 0 and args.path == "grid":
@@ -499,11 +608,7 @@ def main(argv=None):
             "step_ms": {"median": float(np.median(step_ms)), "p99": float(np.percentile(step_ms, 99)),
                         "min": float(np.min(step_ms)), "max": float(np.max(step_ms))},
             "dtype": "f32 arithmetic on " + str(vol.dtype) + " voxels", "data": "synthetic",
-            "config": {"workload": args.workload + (f"@{args.size}" if args.size else ""), "desc": wl["desc"],
-                       "contours": C.count, "samples": wl["N"],
-                       "iterations": wl["T"], "path": args.path, "stopping_rules": rules or None,
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"replicas x{world}"},
+            "config": image_config(args, wl, C.count, world),
             "voxels_per_s": world * int(np.prod(vol.shape)) / (t_ms * 1e-3),
             "evolve_samples_per_s": world * samples / (k_ms * 1e-3),
             "contour_iterations_per_s": world * citers / (t_ms * 1e-3),
@@ -794,8 +899,8 @@ def reference_arm(args, wl, rank, world):
             "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "contours": C, "samples": wl["N"],
-                       "iterations": wl["T"]},
+            "config": image_config(args, wl, C, world) if args.workload not in ("batch-3d", "serve-3d") else
+            {"workload": args.workload, "desc": wl["desc"], "contours": C, "samples": wl["N"], "iterations": wl["T"]},
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": thr, "kind": "oracle",
                              "sample": f"per step: {desc}"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -265,11 +265,13 @@ ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_evolve_params
  * AC_STATIC_SCRATCH_BYTES that every GPU using the library holds until the
  * process exits.  The paper has no counterpart: it describes no memory
  * management.
- *   volume_dev   voxels on the current device, element strides (1, row_stride,
- *                plane_stride) (0 = dense); the brick path needs a 16-byte
- *                aligned base and row/plane strides that are multiples of 16
- *                bytes (AC_PATH_PLAIN takes any layout)
- *   state_dev    5 x n_contours float32 (cx[], cy[], cz[], R[], E[]), updated in
+ *   volume_dev   voxels in device memory of the current device (or managed
+ *                memory), element strides (1, row_stride, plane_stride) (0 =
+ *                dense); the brick path needs a 16-byte aligned base and
+ *                row/plane strides that are multiples of 16 bytes (AC_PATH_PLAIN
+ *                takes any layout)
+ *   state_dev    5 x n_contours float32 (cx[], cy[], cz[], R[], E[]) in device
+ *                memory of the current device (or managed memory), updated in
  *                place; 1 <= n_contours <= AC_STATIC_MAX_CONTOURS
  *   r0, stride   radius and lattice spacing the contours were seeded with (they
  *                size the bricks), > 0
@@ -354,6 +356,20 @@ ac_status ac_evolve_stops(ac_contours *ctr, int64_t counts[2], void *cuda_stream
  * global fallback (ball outside the staged region; plain path: every one).
  * Synchronizes the stream.  Errors: AC_ERR_ARG, AC_ERR_CUDA. */
 ac_status ac_evolve_stats(ac_contours *ctr, int64_t counts[3], void *cuda_stream);
+
+/*
+ * ac_set_wait_limits -- lower the bounds of the library's device waits, process
+ * wide, so that a test can make a wait give up without faulting or hanging the
+ * GPU (the paper has no counterpart).  tma_polls: polls of the first wait of the
+ * brick kernel for a brick's TMA load before it gives up (0: give up at once); a
+ * brick that gives up records AC_ERR_TIMEOUT in its set's status word, still waits
+ * (with the default bound) for its copy in flight, and skips its contours.
+ * localize_rounds: rounds of the overlap competition after which ac_localize
+ * returns AC_ERR_TIMEOUT (0: before the first round).  A negative value restores
+ * the default (2^22 polls; n + 8 rounds for n survivors, which always suffice).
+ * Plans and launches prepared afterwards use the new bound.  Always AC_OK.
+ */
+ac_status ac_set_wait_limits(int64_t tma_polls, int64_t localize_rounds);
 
 /* Number of the library's own kernel launches since it was loaded (all threads).
  * Sorting and selection steps run CUB library kernels, which are not counted. */

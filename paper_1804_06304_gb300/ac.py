@@ -120,6 +120,7 @@ _SIGS = {
     "ac_destroy_plan": (None, [ct.c_void_p]),
     "ac_autotune": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int32, ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_last_error": (ct.c_char_p, []),
+    "ac_set_wait_limits": (ct.c_int, [ct.c_int64, ct.c_int64]),
     "ac_server_create": (ct.c_int, [ct.POINTER(ac_server_params), ct.POINTER(ct.c_void_p)]),
     "ac_server_submit": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
                                     ct.POINTER(ct.c_float), ct.c_float, ct.c_uint32, ct.POINTER(ct.c_int64)]),
@@ -501,13 +502,26 @@ def ac_evolve_static(volume_dev, state_dev, params: EvolveParams, r0: float, str
     (CUDA tensor, [z, y, x] or [y, x]) and ``state_dev`` (CUDA float32 tensor of
     shape (5, C), updated in place) belong to the caller; the library's temporaries
     live in its fixed device array.  Synchronizes the stream."""
+    import torch
+    if not (isinstance(volume_dev, torch.Tensor) and volume_dev.is_cuda):
+        raise ACError(AC_ERR_ARG, "ac_evolve_static: volume_dev must be a CUDA tensor")
+    if not (isinstance(state_dev, torch.Tensor) and state_dev.is_cuda and state_dev.dtype == torch.float32 and
+            state_dev.dim() == 2 and state_dev.shape[0] == 5 and state_dev.is_contiguous()):
+        raise ACError(AC_ERR_ARG, "ac_evolve_static: state_dev must be a contiguous CUDA float32 tensor of shape (5, C)")
+    if volume_dev.device != state_dev.device:
+        raise ACError(AC_ERR_ARG, "ac_evolve_static: volume_dev and state_dev must be on the same device")
     ptr, on_dev, code, shape, strides = _ptr(volume_dev)
     if dtype is not None:
         code = dtype
     ndim = len(shape)
+    if ndim not in (2, 3) or strides[-1] != 1 or code is None:
+        raise ACError(AC_ERR_ARG, "ac_evolve_static: volume_dev must be 2D or 3D with unit x stride and a "
+                                  "uint8 / uint16 (int16) / float16 / float32 dtype")
     dims = (ct.c_int64 * 3)(*(list(shape[::-1]) + [1] * (3 - ndim)))
     sp = (ct.c_float * 3)(*[float(v) for v in (list(spacing) + [1.0] * 3)[:3]])
     C = int(state_dev.shape[1]) if n_contours is None else int(n_contours)
+    if C < 1 or (C > int(state_dev.shape[1]) and C <= AC_STATIC_MAX_CONTOURS):
+        raise ACError(AC_ERR_ARG, "ac_evolve_static: need 1 <= n_contours <= state_dev.shape[1]")
     p = params.to_c()
     _check(load().ac_evolve_static(ct.c_void_p(ptr), code, ndim, dims, strides[-2], strides[-3] if ndim == 3 else 0,
                                    sp, intensity_scale, ct.c_void_p(state_dev.data_ptr()), C, float(r0), float(stride),
@@ -516,6 +530,13 @@ def ac_evolve_static(volume_dev, state_dev, params: EvolveParams, r0: float, str
 
 def ac_last_error() -> str:
     return load().ac_last_error().decode()
+
+
+def ac_set_wait_limits(tma_polls: int = -1, localize_rounds: int = -1):
+    """Lower the bounds of the device waits (testing): polls of the brick kernel's
+    first wait for its TMA load and rounds of the overlap competition; -1 restores
+    the defaults."""
+    _check(load().ac_set_wait_limits(int(tma_polls), int(localize_rounds)))
 
 
 # ------------------------------------------------------------------------ serving form

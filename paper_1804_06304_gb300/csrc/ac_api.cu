@@ -47,6 +47,26 @@ static int elem_size(ac_dtype t)
 
 extern "C" const char *ac_last_error(void) { return g_err.c_str(); }
 
+// Wait bounds that tests may shorten (ac_set_wait_limits); negative = default.
+static std::atomic<int64_t> g_tma_polls{-1};
+static std::atomic<int64_t> g_localize_rounds{-1};
+uint32_t ac::tma_poll_limit()
+{
+    const int64_t v = g_tma_polls.load();
+    return v < 0 ? TMA_POLLS_DEFAULT : (uint32_t)std::min<int64_t>(v, TMA_POLLS_DEFAULT);
+}
+int64_t ac::localize_round_limit(int64_t n)
+{
+    const int64_t v = g_localize_rounds.load();
+    return v < 0 ? n + 8 : v;
+}
+extern "C" ac_status ac_set_wait_limits(int64_t tma_polls, int64_t localize_rounds)
+{
+    g_tma_polls.store(tma_polls < 0 ? -1 : tma_polls);
+    g_localize_rounds.store(localize_rounds < 0 ? -1 : localize_rounds);
+    return AC_OK;
+}
+
 extern "C" int64_t ac_kernel_launches(void) { return g_launches.load(); }
 
 // Clamp a centre coordinate into the box of voxel centres of one axis.
@@ -808,6 +828,7 @@ ac_status prepare_sets(ac_contours *const *sets, const ac_batch_item *items, int
         a.cull_E = p->cull_E;
     }
     a.path_counts = sets[0]->path_counts;
+    a.tma_polls = tma_poll_limit();
     if (pl.grid)   // bounded work per evaluation
         for (int i = 0; i < n_sets; ++i)
             for (int d = 0; d < sets[i]->vol->ndim; ++d) {
@@ -1108,6 +1129,10 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
                             "strides that are multiples of 16 bytes (use AC_PATH_PLAIN otherwise)");
     if (brick && (!(r0 > 0.0f) || !(stride > 0.0f)))
         AC_FAIL(AC_ERR_ARG, "ac_evolve_static: r0 and stride must be positive");
+    int dev = 0;
+    AC_CUDA(cudaGetDevice(&dev));
+    // both buffers must be memory this device's kernels may read: device memory of
+    // this device (a peer's would be read with this device's scratch) or managed
     cudaPointerAttributes pa;
     for (const void *q : {volume_dev, (const void *)state_dev}) {
         if (cudaPointerGetAttributes(&pa, q) != cudaSuccess ||
@@ -1115,9 +1140,10 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
             cudaGetLastError();
             AC_FAIL(AC_ERR_ARG, "ac_evolve_static: volume and state must be device memory");
         }
+        if (pa.type == cudaMemoryTypeDevice && pa.device != dev)
+            AC_FAIL(AC_ERR_ARG, "ac_evolve_static: volume and state must be memory of the current device (device " +
+                                    std::to_string(dev) + "), not of device " + std::to_string(pa.device));
     }
-    int dev = 0;
-    AC_CUDA(cudaGetDevice(&dev));
     unsigned char *base = nullptr;
     s = static_scratch_ptr(dev, &base);
     if (s != AC_OK) return s;
@@ -1170,6 +1196,7 @@ extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, in
         a.vol_coef = (float)((ndim == 3 ? 4.0 / 3.0 * M_PI : M_PI) / p->N);
     }
     a.path_counts = ctr.path_counts;
+    a.tma_polls = tma_poll_limit();
 
     VolDesc desc = make_desc(&ctr, p->stream_id);
     desc.first_iter = a.first_iter;

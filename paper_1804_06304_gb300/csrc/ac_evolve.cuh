@@ -668,17 +668,26 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
     const int r0[3] = {max(0, bxi * a.B[0] - a.halo[0]) / AL * AL, max(0, byi * a.B[1] - a.halo[1]),
                        DIM == 3 ? max(0, bzi * a.B[2] - a.halo[2]) : 0};
 
+    // One thread issues the load and decides whether it landed within the bound, so
+    // every thread of the CTA takes the same branch.  On giving up it records the
+    // timeout and waits (again bounded) for the copy in flight, so that no copy is
+    // still writing shared memory when the CTA exits.
+    __shared__ int landed;
     if (threadIdx.x == 0) mbar_init(&mbar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(&mbar, (uint32_t)a.raw_bytes);
         tma_load_3d(smem_raw, &a.tmaps[v], r0[0], r0[1], r0[2], &mbar);
+        landed = mbar_wait_bounded(&mbar, 0, a.tma_polls) ? 1 : 0;
+        if (!landed) {
+            atomicOr(V.status, STATUS_TMA_TIMEOUT);
+            mbar_wait_bounded(&mbar, 0, TMA_DRAIN_POLLS);
+        }
     }
-    if (!mbar_wait_bounded(&mbar, 0, 1u << 22)) {
-        if (threadIdx.x == 0) atomicOr(V.status, STATUS_TMA_TIMEOUT);
-        mbar_wait_bounded(&mbar, 0, 1u << 22);   // let an in-flight copy land before exit
-        return;
-    }
+    __syncthreads();
+    if (!landed) return;
+    // each thread observes the completed phase itself (at once) before reading the region
+    mbar_wait_bounded(&mbar, 0, TMA_DRAIN_POLLS);
     const T *reg = reinterpret_cast<const T *>(smem_raw);
     const bool quad = DIM == 2 && a.quad_off > 0;
     QT *Q = reinterpret_cast<QT *>(smem_raw + a.quad_off);

@@ -108,6 +108,11 @@ cudaError_t launch_grid(ac_dtype t, const EvolveArgs &a, int G, bool comp, int w
 // the argument checks of ac_evolve (ac_api.cu)
 ac_status check_evolve_params(const ac_evolve_params *p);
 
+// bounds of the device waits (ac_set_wait_limits): polls of the first wait for a
+// brick's TMA load, and localization rounds for n survivors
+uint32_t tma_poll_limit();
+int64_t localize_round_limit(int64_t n);
+
 // localization (ac_localize.cu); returns an ac_status and sets the message
 ac_status localize_impl(ac_contours *ctr, float E0, ac_cell *out_host, int64_t cap, int64_t *n_out,
                         cudaStream_t st);

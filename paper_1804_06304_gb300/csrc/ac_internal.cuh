@@ -37,6 +37,11 @@ template <typename I> __device__ __forceinline__ I checked(I i, I n, int32_t *st
     return i;
 }
 
+// Polls of the bounded mbarrier waits of the brick kernel: the first wait for a
+// brick's TMA load (unless a test shortens it) and the drain wait after giving up.
+constexpr uint32_t TMA_POLLS_DEFAULT = 1u << 22;
+constexpr uint32_t TMA_DRAIN_POLLS = 1u << 22;
+
 // Grid path: largest ball radius, in voxels along any axis, that an evaluation
 // may cover (bounds the work of one evaluation).
 constexpr float GRID_MAX_RADIUS_VOXELS = 256.0f;
@@ -111,6 +116,7 @@ struct EvolveArgs {
     float *trace;        // optional (volume 0 only)
     int64_t tk0, tk1;
     int32_t tt0, tt1;
+    uint32_t tma_polls;  // polls of the first wait for a brick's TMA load (then it gives up)
     unsigned long long *path_counts;   // [3]: fast, clamped, global contour-iterations
     const uint32_t *active;            // plain path: contours to visit (nullptr: all)
     const unsigned long long *n_active;// device count of `active`

@@ -9,6 +9,7 @@
 // as one of them is accepted (the lexicographically first maximal independent
 // set).  Neighbours are found through a uniform grid of cell size
 // rho max(R), built with a sort.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <cub/cub.cuh>
@@ -270,25 +271,29 @@ ac_status localize_impl(ac_contours *ctr, float E0, ac_cell *out_host, int64_t c
     LC_CUDA(sc.stat.ensure(n));
     uint8_t *status = sc.stat.as<uint8_t>();
     LC_CUDA(cudaMemsetAsync(status, UNDECIDED, n, st));
-    const int64_t max_rounds = n + 8;
+    // every round decides at least the undecided survivor of highest priority, so n
+    // rounds always settle it; the bound (n + 8 unless a test lowers it) is checked
+    // between batches of up to 8 rounds
+    const int64_t max_rounds = localize_round_limit(n);
     int64_t rounds = 0;
-    for (;;) {
-        for (int r = 0; r < 8; ++r, ++rounds) {
+    int32_t und = (int32_t)n;
+    while (und > 0) {
+        if (rounds >= max_rounds) {
+            const int32_t bit = STATUS_LOCALIZE_LIMIT;
+            LC_CUDA(cudaMemcpyAsync(ctr->status, &bit, sizeof(bit), cudaMemcpyHostToDevice, st));
+            LC_CUDA(cudaStreamSynchronize(st));
+            LC_FAIL(AC_ERR_TIMEOUT, "ac_localize: competition did not settle within its round bound");
+        }
+        const int64_t batch = std::min<int64_t>(8, max_rounds - rounds);
+        for (int64_t r = 0; r < batch; ++r, ++rounds) {
             LC_CUDA(cudaMemsetAsync(cnt + 2, 0, sizeof(int32_t), st));
             round_kernel<<<blocks_for(n), 256, 0, st>>>(pos, n, g, sc.cell_start.as<int32_t>(), sc.celli_s.as<uint32_t>(),
                                                         rho, status, cnt + 2);
             count_launch();
             LC_CUDA(cudaGetLastError());
         }
-        int32_t und = 0;
         LC_CUDA(cudaMemcpyAsync(&und, cnt + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         LC_CUDA(cudaStreamSynchronize(st));
-        if (und == 0) break;
-        if (rounds >= max_rounds) {
-            int32_t bit = STATUS_LOCALIZE_LIMIT;
-            cudaMemcpy(ctr->status, &bit, sizeof(bit), cudaMemcpyHostToDevice);
-            LC_FAIL(AC_ERR_TIMEOUT, "ac_localize: competition did not settle within its round bound");
-        }
     }
 
     // 5. kept contours in priority (= acceptance) order

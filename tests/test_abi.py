@@ -58,6 +58,7 @@ def test_argument_validation_without_device(ac):
     assert l.ac_set_state(None, None, None) == ac.AC_ERR_ARG
     assert l.ac_philox4x32_10(None, 0, None, -1, None) == ac.AC_ERR_ARG
     assert l.ac_contour_count(None) == -1
+    assert l.ac_set_wait_limits(-1, -1) == ac.AC_OK
     l.ac_destroy_volume(None)
     l.ac_destroy_contours(None)
 

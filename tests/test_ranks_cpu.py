@@ -90,3 +90,25 @@ def test_oracle_check_measures_centre_error_in_voxels():
     assert chk["frac_centre_within_0.25_voxel"] == 0.75      # 0.25 voxel passes, 0.6 does not
     conv = bench.oracle_check(moved, idx, cR, E, (1.0, 1.0, 2.0), 3, E0=float(np.sort(E)[2]))
     assert conv["converged"]["contours"] == 2
+
+
+def test_oracle_check_detection_agreement():
+    """The bench's detection-set agreement: the oracle's own localization of its
+    states against given cells, one-to-one within 0.5 voxel (anisotropic spacing)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle
+    # three well separated contours, all below E0; the GPU side finds two of them,
+    # one shifted by 0.4 voxel along z (0.8 physical units at spacing 2)
+    cR = np.array([[10.0, 10.0, 10.0, 3.0], [30.0, 10.0, 10.0, 3.0], [10.0, 30.0, 20.0, 3.0]])
+    E = np.array([-5.0, -4.0, -3.0])
+    state = np.vstack([cR.T, E]).astype(np.float32)
+    idx = np.arange(3)
+    cells = np.array([[10.0, 10.0, 10.8], [30.0, 10.0, 10.0]])
+    chk = bench.oracle_check(state, idx, cR, E, (1.0, 1.0, 2.0), 3, E0=-1.0, gpu_cells=cells)
+    assert list(oracle.localize(3, cR, E, -1.0)) == [0, 1, 2]
+    assert chk["detections"] == {"gpu": 2, "oracle": 3, "matched": 2, "agreement": 0.8}
+    far = np.array([[10.0, 10.0, 12.2], [30.0, 10.0, 10.0], [10.0, 30.0, 20.0]])   # 1.1 voxel off in z
+    assert bench.oracle_check(state, idx, cR, E, (1.0, 1.0, 2.0), 3, E0=-1.0,
+                              gpu_cells=far)["detections"]["matched"] == 2
