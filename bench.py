@@ -75,12 +75,13 @@ WORKLOADS = {
                           "r 3-8; stride-4 lattices; one autotuned plan over all volumes replayed as a CUDA graph; "
                           "256 samples, 80 iterations"),
     "serve-3d": dict(ndim=3, stride=6.0, N=512, T=100, seed=4, tiles=8, requests=32, load=0.7, ipr=10,
-                     budget_gb=120, contour_cap=262144,
+                     budget_gb=120, contour_cap=262144, bound_budget_gb=0.4,
                      desc="request loop over uint16 tiles 128^3..1024x1024x64 (log-uniform voxel count, brain-3d "
                           "nucleus model, 8 distinct tiles cycled with distinct Philox streams), 32 requests; "
                           "saturated (all submitted at once) and Poisson arrivals at 0.7x the saturated rate; "
                           "HBM budget 120 GB, at most 262,144 resident contours, 10 iterations per round (up "
-                          "to 8x for small tiles); 512 samples, 100 iterations"),
+                          "to 8x for small tiles); 512 samples, 100 iterations; also saturated under a 0.4 GB "
+                          "budget without the contour cap"),
 }
 
 
@@ -779,8 +780,8 @@ def serve_arm(args, wl, rank, world, dev):
         return int(np.prod([max(1, int(math.floor(n * sp / wl["stride"]))) for n, sp in
                             zip(t.shape_xyz, t.spacing)]))
 
-    def run(arrivals, cap=wl["contour_cap"], balance=True):
-        srv = ac.Server(params, ac.AC_U16, 3, wl["stride"], E0, hbm_budget_bytes=int(wl["budget_gb"] * 1e9),
+    def run(arrivals, cap=wl["contour_cap"], balance=True, budget_gb=wl["budget_gb"]):
+        srv = ac.Server(params, ac.AC_U16, 3, wl["stride"], E0, hbm_budget_bytes=int(budget_gb * 1e9),
                         iters_per_round=wl["ipr"], max_resident_contours=cap, balance_rounds=balance)
         t0 = time.perf_counter()
         tickets = []
@@ -820,6 +821,10 @@ def serve_arm(args, wl, rank, world, dev):
     # the same Poisson stream with every tile advancing iters_per_round per round
     _, _, _, res_nb, _ = run(arrivals, balance=False)
     lat_nb = np.array([r["total_ms"] for r in res_nb])
+    # the saturated stream under a budget below its working set (no contour cap):
+    # admission by device bytes alone
+    wall_b, samples_b, _, res_b, st_b = run([0.0] * n_req, cap=0, budget_gb=wl["bound_budget_gb"])
+    lat_b = np.array([r["total_ms"] for r in res_b])
     reducer = torch_max_reducer(dev) if dist_on else None
     t_ms, value = aggregate_ranks([wall * 1e3], samples, world, reducer)
     lat = np.array([r["total_ms"] for r in res_p])
@@ -854,7 +859,13 @@ def serve_arm(args, wl, rank, world, dev):
                                                       "latency_ms_p99": float(np.percentile(lat_nb, 99))},
                         "uncapped_saturated": {"samples_per_s": samples_u / wall_u,
                                                "latency_ms_p50": float(np.percentile(lat_u, 50)),
-                                               "latency_ms_p99": float(np.percentile(lat_u, 99))}},
+                                               "latency_ms_p99": float(np.percentile(lat_u, 99))},
+                        "budget_bound_saturated": {"budget_gb": wl["bound_budget_gb"],
+                                                   "peak_resident_gb": st_b["peak_resident_bytes"] / 1e9,
+                                                   "working_set_gb": sum(r["est_bytes"] for r in res_b) / 1e9,
+                                                   "samples_per_s": samples_b / wall_b,
+                                                   "latency_ms_p50": float(np.percentile(lat_b, 50)),
+                                                   "latency_ms_p99": float(np.percentile(lat_b, 99))}},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s",
                          "frac": achieved / peak, "traffic": None,

@@ -226,8 +226,11 @@ ac_status ac_evolve_batch(ac_contours *const *sets, const ac_batch_item *items, 
  * and stream words for later launches (a plain-path graph is recaptured when the
  * iteration span changes).  ac_plan_rebind replaces the plan's sets (and their
  * items) for later launches, keeping the plan's parameters and reusing its device
- * buffers, which only grow; it drops the captured graph, uploads on the stream and
- * does not synchronize.  After a failed rebind the plan has no sets and its
+ * buffers, which only grow; it uploads on the stream and does not synchronize.
+ * After a rebind (or an item change that alters the launches) the next launch
+ * with use_graph = 1 captures again and updates the executable graph in place
+ * (cudaGraphExecUpdate) when the launches keep their topology, or instantiates a
+ * new one.  After a failed rebind the plan has no sets and its
  * launches return AC_ERR_STATE until a rebind succeeds.  The sets, their volumes
  * and the plan's own buffers must stay alive and unmoved while the plan launches
  * on them; launches on one plan are serialised by the caller's stream.

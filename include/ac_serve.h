@@ -9,13 +9,19 @@
  *
  * A native worker thread runs rounds.  In every round each resident tile advances
  * `iters_per_round` iterations (fewer in its last round) through one batched
- * launch over all resident tiles (an ac_plan; the per-tile iteration windows of
- * ac_batch_item).  Between rounds, waiting tiles are admitted in arrival order
- * while the estimated device bytes of the resident tiles stay within
- * `hbm_budget_bytes`, and tiles that finished are localized, their cells kept for
- * the caller, and their device memory released (a tile is admitted when it fits
- * the byte budget, the tile cap and the contour cap; the first tile in line is
- * always admitted when nothing is resident).  Because the Philox counters of a
+ * launch over all resident tiles (an ac_plan, replayed as a CUDA graph that is
+ * updated in place when the resident set changes; the per-tile iteration windows
+ * of ac_batch_item).  Between rounds, waiting tiles are admitted in arrival order
+ * while the estimated device bytes of the resident and not yet released tiles
+ * stay within `hbm_budget_bytes` (a tile is admitted when it fits the byte
+ * budget, the tile cap and the contour cap; the first tile in line is always
+ * admitted when nothing is resident).  The work overlaps on three streams of the
+ * server: admitted tiles are uploaded and seeded on an upload stream while the
+ * current round runs (the round stream waits on an event before the tile's first
+ * round); the tiles a round finishes are localized, their cells kept for the
+ * caller, on a localization stream while the next round runs; tile memory comes
+ * from a stream-ordered pool of the server (caching up to the budget), so
+ * neither admission nor release synchronizes the device.  Because the Philox counters of a
  * sample are (block, n, k, stream_id) with one key for the server, a tile's cells and
  * energies do not depend on which tiles it shared rounds with: they equal those
  * of ac_evolve on that tile alone with the server's evolve parameters and the
@@ -106,6 +112,22 @@ ac_status ac_server_create(const ac_server_params *params, ac_server **out);
 ac_status ac_server_submit(ac_server *srv, const void *data_host, const int64_t dims[3], int64_t row_stride,
                            int64_t plane_stride, const float spacing[3], float intensity_scale, uint32_t stream_id,
                            int64_t *ticket);
+
+/*
+ * ac_server_submit_traced -- ac_server_submit that also records the tile's
+ * evaluations in `trace` (as ac_evolve's trace: device buffer of (t_end - t_begin)
+ * x (k_end - k_begin) x 9 floats for the tile's contours k in [k_begin, k_end) and
+ * iterations n in [t_begin, t_end), 1 <= t_begin, t_end <= T + 1), so that a served
+ * tile can be checked evaluation by evaluation like a tile evolved alone.  The
+ * buffer must stay valid until ac_server_wait has returned for the ticket.  One
+ * traced tile is resident at a time (a second one waits for the first to finish),
+ * and rounds with a traced tile are launched without graph replay.  trace NULL:
+ * ac_server_submit.  Errors: those of ac_server_submit; AC_ERR_ARG for a trace
+ * range outside the tile's lattice or the server's iterations.
+ */
+ac_status ac_server_submit_traced(ac_server *srv, const void *data_host, const int64_t dims[3], int64_t row_stride,
+                                  int64_t plane_stride, const float spacing[3], float intensity_scale,
+                                  uint32_t stream_id, const ac_trace *trace, int64_t *ticket);
 
 /*
  * ac_server_wait -- wait up to `timeout_s` seconds (< 0: forever, 0: poll) for a

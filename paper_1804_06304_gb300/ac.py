@@ -124,6 +124,9 @@ _SIGS = {
     "ac_server_create": (ct.c_int, [ct.POINTER(ac_server_params), ct.POINTER(ct.c_void_p)]),
     "ac_server_submit": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
                                     ct.POINTER(ct.c_float), ct.c_float, ct.c_uint32, ct.POINTER(ct.c_int64)]),
+    "ac_server_submit_traced": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
+                                           ct.POINTER(ct.c_float), ct.c_float, ct.c_uint32, ct.POINTER(ac_trace),
+                                           ct.POINTER(ct.c_int64)]),
     "ac_server_wait": (ct.c_int, [ct.c_void_p, ct.c_int64, ct.c_double, ct.c_void_p, ct.c_int64,
                                   ct.POINTER(ac_tile_result)]),
     "ac_server_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_server_stats)]),
@@ -563,8 +566,10 @@ class Server:
         self.ndim, self.stride = int(ndim), float(stride)
 
     def submit(self, volume: np.ndarray, spacing=(1.0, 1.0, 1.0), intensity_scale: float = 1.0,
-               stream_id: int = 0) -> int:
-        """``volume`` indexed [z, y, x] (3D) or [y, x] (2D), host memory, x fastest."""
+               stream_id: int = 0, trace=None) -> int:
+        """``volume`` indexed [z, y, x] (3D) or [y, x] (2D), host memory, x fastest.
+        ``trace`` = (device tensor, k0, k1, t0, t1) records the tile's evaluations as
+        ac_evolve's trace does (ac_server_submit_traced)."""
         a = np.asarray(volume)
         ptr, _, _, shape, strides = _ptr(a)
         if strides[-1] != 1 or len(shape) not in (2, 3):
@@ -572,10 +577,15 @@ class Server:
         dims = (ct.c_int64 * 3)(*(list(shape[::-1]) + [1] * (3 - len(shape))))
         sp = (ct.c_float * 3)(*[float(s) for s in (list(spacing) + [1.0] * 3)[:3]])
         t = ct.c_int64()
-        _check(load().ac_server_submit(self.handle, ct.c_void_p(ptr), dims, strides[-2],
-                                       strides[-3] if len(shape) == 3 else 0, sp, float(intensity_scale),
-                                       int(stream_id), ct.byref(t)))
-        self._arrays[t.value] = a
+        tr = None
+        if trace is not None:
+            buf, k0, k1, t0, t1 = trace
+            tr = ac_trace(ct.c_void_p(buf.data_ptr()), int(k0), int(k1), int(t0), int(t1))
+        _check(load().ac_server_submit_traced(self.handle, ct.c_void_p(ptr), dims, strides[-2],
+                                              strides[-3] if len(shape) == 3 else 0, sp, float(intensity_scale),
+                                              int(stream_id), ct.byref(tr) if tr is not None else None,
+                                              ct.byref(t)))
+        self._arrays[t.value] = (a, trace)
         lattice = 1
         for d in range(self.ndim):   # ac_seed's lattice size bounds the number of cells
             lattice *= max(1, int(math.floor(dims[d] * sp[d] / self.stride)))

@@ -98,14 +98,23 @@ static cudaError_t copy_voxels(const ac_volume *v, const void *data, int data_on
     return e;
 }
 
-// ------------------------------------------------------------------ volume
-extern "C" ac_status ac_create_volume(const void *data, int data_on_device, ac_dtype dtype, int ndim,
-                                      const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
-                                      const float spacing[3], float intensity_scale, void *cuda_stream,
-                                      ac_volume **out)
+// Device allocation: stream-ordered from `pool` on `st`, or plain cudaMalloc.
+static cudaError_t dev_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t st)
 {
-    ac::Range nvtx_range("ac_create_volume");
-    g_err.clear();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMalloc(p, bytes);
+}
+static void dev_free(void *p, cudaMemPool_t pool, cudaStream_t st)
+{
+    if (!p) return;
+    if (pool) cudaFreeAsync(p, st);
+    else cudaFree(p);
+}
+
+// ------------------------------------------------------------------ volume
+static ac_status create_volume_impl(cudaMemPool_t pool, const void *data, int data_on_device, ac_dtype dtype,
+                                    int ndim, const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
+                                    const float spacing[3], float intensity_scale, cudaStream_t st, ac_volume **out)
+{
     if (!out) AC_FAIL(AC_ERR_ARG, "ac_create_volume: out is NULL");
     *out = nullptr;
     if (!data || !dims || !spacing) AC_FAIL(AC_ERR_ARG, "ac_create_volume: NULL data, dims or spacing");
@@ -140,20 +149,40 @@ extern "C" ac_status ac_create_volume(const void *data, int data_on_device, ac_d
     v->pitch_y = (int64_t)(pitch / es);
     v->pitch_z = v->pitch_y * n[1];
     v->bytes = pitch * (size_t)n[1] * (size_t)n[2];
-    cudaError_t e = cudaMalloc(&v->data, v->bytes);
+    v->pool = pool;
+    cudaError_t e = dev_alloc(&v->data, v->bytes, pool, st);
     if (e != cudaSuccess) {
         delete v;
         AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
-                std::string("ac_create_volume: cudaMalloc: ") + cudaGetErrorString(e));
+                std::string("ac_create_volume: allocation: ") + cudaGetErrorString(e));
     }
-    e = copy_voxels(v, data, data_on_device, row_stride, plane_stride, (cudaStream_t)cuda_stream);
+    e = copy_voxels(v, data, data_on_device, row_stride, plane_stride, st);
     if (e != cudaSuccess) {
-        cudaFree(v->data);
+        dev_free(v->data, pool, st);
         delete v;
         AC_FAIL(AC_ERR_CUDA, std::string("ac_create_volume: copy: ") + cudaGetErrorString(e));
     }
     *out = v;
     return AC_OK;
+}
+
+extern "C" ac_status ac_create_volume(const void *data, int data_on_device, ac_dtype dtype, int ndim,
+                                      const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
+                                      const float spacing[3], float intensity_scale, void *cuda_stream,
+                                      ac_volume **out)
+{
+    ac::Range nvtx_range("ac_create_volume");
+    g_err.clear();
+    return create_volume_impl(nullptr, data, data_on_device, dtype, ndim, dims, row_stride, plane_stride, spacing,
+                              intensity_scale, (cudaStream_t)cuda_stream, out);
+}
+
+ac_status ac::create_volume_pooled(cudaMemPool_t pool, const void *data, int data_on_device, ac_dtype dtype,
+                                   int ndim, const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
+                                   const float spacing[3], float intensity_scale, cudaStream_t st, ac_volume **out)
+{
+    return create_volume_impl(pool, data, data_on_device, dtype, ndim, dims, row_stride, plane_stride, spacing,
+                              intensity_scale, st, out);
 }
 
 extern "C" ac_status ac_load_volume(ac_volume *vol, const void *data, int data_on_device, int64_t row_stride,
@@ -170,12 +199,14 @@ extern "C" ac_status ac_load_volume(ac_volume *vol, const void *data, int data_o
     return AC_OK;
 }
 
-extern "C" void ac_destroy_volume(ac_volume *vol)
+void ac::destroy_volume_on(ac_volume *vol, cudaStream_t st)
 {
     if (!vol) return;
-    cudaFree(vol->data);
+    dev_free(vol->data, vol->pool, st);
     delete vol;
 }
+
+extern "C" void ac_destroy_volume(ac_volume *vol) { ac::destroy_volume_on(vol, nullptr); }
 
 // ------------------------------------------------------------------ seeding
 __global__ void seed_lattice_kernel(float *state, int64_t C, int Lx, int Ly, float fx, float fy, float fz,
@@ -191,23 +222,29 @@ __global__ void seed_lattice_kernel(float *state, int64_t C, int Lx, int Ly, flo
     }
 }
 
-static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out)
+// Contour set of C contours on `vol`: state, status word, hold words and path
+// counters (zeroed), allocated plainly or, with a pool, in stream order on `st`.
+static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out, cudaMemPool_t pool = nullptr,
+                               cudaStream_t st = nullptr)
 {
     ac_contours *c = new ac_contours();
     c->vol = vol;
     c->C = C;
-    cudaError_t e = cudaMalloc(&c->state, sizeof(float) * 5 * (size_t)(C > 0 ? C : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int32_t) * 4);
-    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int32_t) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->hold, sizeof(int32_t) * (size_t)(C > 0 ? C : 1));
-    if (e == cudaSuccess) e = cudaMemset(c->hold, 0, sizeof(int32_t) * (size_t)(C > 0 ? C : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->path_counts, sizeof(unsigned long long) * 4);
-    if (e == cudaSuccess) e = cudaMemset(c->path_counts, 0, sizeof(unsigned long long) * 4);
+    c->pool = pool;
+    auto zero = [&](void *p, size_t n) { return pool ? cudaMemsetAsync(p, 0, n, st) : cudaMemset(p, 0, n); };
+    const size_t cn = (size_t)(C > 0 ? C : 1);
+    cudaError_t e = dev_alloc((void **)&c->state, sizeof(float) * 5 * cn, pool, st);
+    if (e == cudaSuccess) e = dev_alloc((void **)&c->status, sizeof(int32_t) * 4, pool, st);
+    if (e == cudaSuccess) e = zero(c->status, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = dev_alloc((void **)&c->hold, sizeof(int32_t) * cn, pool, st);
+    if (e == cudaSuccess) e = zero(c->hold, sizeof(int32_t) * cn);
+    if (e == cudaSuccess) e = dev_alloc((void **)&c->path_counts, sizeof(unsigned long long) * 4, pool, st);
+    if (e == cudaSuccess) e = zero(c->path_counts, sizeof(unsigned long long) * 4);
     if (e != cudaSuccess) {
-        if (c->state) cudaFree(c->state);
-        if (c->status) cudaFree(c->status);
-        if (c->hold) cudaFree(c->hold);
-        if (c->path_counts) cudaFree(c->path_counts);
+        dev_free(c->state, pool, st);
+        dev_free(c->status, pool, st);
+        dev_free(c->hold, pool, st);
+        dev_free(c->path_counts, pool, st);
         delete c;
         AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
                 std::string("ac_seed: allocation: ") + cudaGetErrorString(e));
@@ -216,11 +253,26 @@ static ac_status make_contours(ac_volume *vol, int64_t C, ac_contours **out)
     return AC_OK;
 }
 
+static ac_status seed_impl(ac_volume *vol, const ac_seed_params *params, const float *explicit_cR,
+                           int64_t n_explicit, void *cuda_stream, ac_contours **out, cudaMemPool_t pool);
+
 extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const float *explicit_cR,
                              int64_t n_explicit, void *cuda_stream, ac_contours **out)
 {
     ac::Range nvtx_range("ac_seed");
     g_err.clear();
+    return seed_impl(vol, params, explicit_cR, n_explicit, cuda_stream, out, nullptr);
+}
+
+ac_status ac::seed_lattice_pooled(cudaMemPool_t pool, ac_volume *vol, const ac_seed_params *params, cudaStream_t st,
+                                  ac_contours **out)
+{
+    return seed_impl(vol, params, nullptr, 0, st, out, pool);
+}
+
+static ac_status seed_impl(ac_volume *vol, const ac_seed_params *params, const float *explicit_cR,
+                           int64_t n_explicit, void *cuda_stream, ac_contours **out, cudaMemPool_t pool)
+{
     if (!out) AC_FAIL(AC_ERR_ARG, "ac_seed: out is NULL");
     *out = nullptr;
     if (!vol) AC_FAIL(AC_ERR_ARG, "ac_seed: vol is NULL");
@@ -278,7 +330,7 @@ extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const
     const int64_t C = L[0] * L[1] * L[2];
     if (C >= ((int64_t)1 << 31)) AC_FAIL(AC_ERR_ARG, "ac_seed: lattice too fine");
     ac_contours *c = nullptr;
-    ac_status rs = make_contours(vol, C, &c);
+    ac_status rs = make_contours(vol, C, &c, pool, (cudaStream_t)cuda_stream);
     if (rs != AC_OK) return rs;
     c->lattice = true;
     for (int d = 0; d < 3; ++d) {
@@ -291,7 +343,7 @@ extern "C" ac_status ac_seed(ac_volume *vol, const ac_seed_params *params, const
     c->stride_hint = s;
     ac_status rs2 = ac_reseed(c, cuda_stream);
     if (rs2 != AC_OK) {
-        ac_destroy_contours(c);
+        ac::destroy_contours_on(c, (cudaStream_t)cuda_stream);
         return rs2;
     }
     *out = c;
@@ -319,18 +371,20 @@ extern "C" ac_status ac_reseed(ac_contours *c, void *cuda_stream)
 
 extern "C" int64_t ac_contour_count(const ac_contours *ctr) { return ctr ? ctr->C : -1; }
 
-extern "C" void ac_destroy_contours(ac_contours *ctr)
+void ac::destroy_contours_on(ac_contours *ctr, cudaStream_t st)
 {
     if (!ctr) return;
     ctr->scratch.release_all();
     if (ctr->ev0) cudaEventDestroy(ctr->ev0);
     if (ctr->ev1) cudaEventDestroy(ctr->ev1);
-    cudaFree(ctr->state);
-    cudaFree(ctr->status);
-    cudaFree(ctr->hold);
-    cudaFree(ctr->path_counts);
+    dev_free(ctr->state, ctr->pool, st);
+    dev_free(ctr->status, ctr->pool, st);
+    dev_free(ctr->hold, ctr->pool, st);
+    dev_free(ctr->path_counts, ctr->pool, st);
     delete ctr;
 }
+
+extern "C" void ac_destroy_contours(ac_contours *ctr) { ac::destroy_contours_on(ctr, nullptr); }
 
 // ------------------------------------------------------------------ state
 static ac_status check_status(ac_contours *ctr, cudaStream_t st)
@@ -1288,6 +1342,7 @@ struct ac_plan {
     int64_t graph_launches = 0;
     int32_t span0 = 0, span1 = 0;   // iteration span the graph was captured with
     bool valid = true;              // false after a failed rebind
+    bool stale = false;             // the launch changed since the graph was captured
 };
 
 static void drop_graph(ac_plan *pl)
@@ -1331,7 +1386,7 @@ extern "C" ac_status ac_plan_rebind(ac_plan *pl, ac_contours *const *sets, const
     g_err.clear();
     if (!pl) AC_FAIL(AC_ERR_ARG, "ac_plan_rebind: NULL plan");
     if (!sets || n_sets < 1 || n_sets > 4096) AC_FAIL(AC_ERR_ARG, "ac_plan_rebind: need 1..4096 sets");
-    drop_graph(pl);
+    pl->stale = true;   // the next graph launch recaptures and updates the executable graph
     pl->valid = false;
     std::vector<ac_contours *> keep(sets, sets + n_sets);
     Prepared pr;
@@ -1358,8 +1413,8 @@ extern "C" ac_status ac_plan_set_items(ac_plan *pl, const ac_batch_item *items, 
     if (s != AC_OK) return s;
     // a captured graph holds one plain launch per iteration of its span (plain path,
     // or the second phase of a split brick launch)
-    if (!pr.pl.brick && !pr.pl.grid && (pr.a.first_iter != pl->span0 || pr.a.last_iter != pl->span1)) drop_graph(pl);
-    if (pr.pl.brick && (was_split != pr.split || p2f != pr.p2_first || p2l != pr.p2_last)) drop_graph(pl);
+    if (!pr.pl.brick && !pr.pl.grid && (pr.a.first_iter != pl->span0 || pr.a.last_iter != pl->span1)) pl->stale = true;
+    if (pr.pl.brick && (was_split != pr.split || p2f != pr.p2_first || p2l != pr.p2_last)) pl->stale = true;
     return AC_OK;
 }
 
@@ -1372,8 +1427,11 @@ extern "C" ac_status ac_plan_launch(ac_plan *pl, int use_graph, void *cuda_strea
     if (pl->pr.total == 0) return AC_OK;   // only empty sets
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!use_graph) return enqueue_prepared(pl->pr, pl->sc, st, nullptr);
-    if (!pl->exec) {
-        // capture once on a stream of the plan's own (the legacy stream cannot capture)
+    if (!pl->exec || pl->stale) {
+        // capture on a stream of the plan's own (the legacy stream cannot capture);
+        // an executable graph from an earlier capture is updated in place when the
+        // new capture has its topology (same launches, other sizes and arguments),
+        // and instantiated afresh otherwise
         if (!pl->cap_stream) AC_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
         AC_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
         int64_t n = 0;
@@ -1385,14 +1443,48 @@ extern "C" ac_status ac_plan_launch(ac_plan *pl, int use_graph, void *cuda_strea
             return s;
         }
         AC_CUDA(e);
+        bool updated = false;
+        if (pl->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(pl->exec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(pl->exec);
+                pl->exec = nullptr;
+            }
+        }
+        if (pl->graph) cudaGraphDestroy(pl->graph);
         pl->graph = g;
-        AC_CUDA(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+        if (!updated) AC_CUDA(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+        pl->stale = false;
         pl->graph_launches = n;
         pl->span0 = pl->pr.a.first_iter;
         pl->span1 = pl->pr.a.last_iter;
     }
     AC_CUDA(cudaGraphLaunch(pl->exec, st));
     count_launch(pl->graph_launches);
+    return AC_OK;
+}
+
+ac_status ac::plan_set_trace(ac_plan *pl, int set, const ac_trace *tr)
+{
+    if (!pl || set < 0 || set >= (int)pl->sets.size()) AC_FAIL(AC_ERR_ARG, "plan_set_trace: bad set");
+    EvolveArgs &a = pl->pr.a;
+    if (!tr || !tr->device_buf) {
+        if (a.trace) pl->stale = true;
+        a.trace = nullptr;
+        return AC_OK;
+    }
+    const ac_contours *c = pl->sets[set];
+    if (tr->k_begin < 0 || tr->k_end > c->C || tr->k_begin > tr->k_end || tr->t_begin < 1 || tr->t_begin > tr->t_end)
+        AC_FAIL(AC_ERR_ARG, "plan_set_trace: trace range outside the contours or iterations");
+    a.trace = tr->device_buf;
+    a.tk0 = tr->k_begin;
+    a.tk1 = tr->k_end;
+    a.tt0 = tr->t_begin;
+    a.tt1 = tr->t_end;
+    a.trace_vol = set;
+    pl->stale = true;
     return AC_OK;
 }
 

@@ -586,7 +586,7 @@ __device__ __forceinline__ bool finite_step(const Step &s)
 __device__ __forceinline__ void write_trace(const EvolveArgs &a, int vol, int64_t k, int n, const float *c, float R,
                                             const Step &s)
 {
-    if (a.trace == nullptr || vol != 0 || k < a.tk0 || k >= a.tk1 || n < a.tt0 || n >= a.tt1) return;
+    if (a.trace == nullptr || vol != a.trace_vol || k < a.tk0 || k >= a.tk1 || n < a.tt0 || n >= a.tt1) return;
     float *t = a.trace + (((int64_t)(n - a.tt0) * (a.tk1 - a.tk0)) + (k - a.tk0)) * 9;
     t[0] = c[0]; t[1] = c[1]; t[2] = c[2]; t[3] = R;
     t[4] = s.E; t[5] = s.dEdR; t[6] = s.g[0]; t[7] = s.g[1]; t[8] = s.g[2];
@@ -705,6 +705,13 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
     }
 
     const int py = a.ext[0], pz = a.ext[0] * a.ext[1];
+    // the staged region's first and last usable tap per axis (within the volume)
+    float fr_lo[3], fr_hi[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        fr_lo[d] = (float)r0[d];
+        fr_hi[d] = (float)min(V.n[d] - 1, r0[d] + a.ext[d] - 1);
+    }
     const int nquads = qp * (a.ext[1] - 1);                       // extents for the checked build
     const int64_t nraw = (int64_t)a.ext[0] * a.ext[1] * a.ext[2];
     const int lig = threadIdx.x % G;
@@ -726,17 +733,31 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
             iter_consts<DIM>(ic, c, R, V, a);
             // where do the taps of the whole ball fall (clamped like the samples)?
             const float Ro = R + 0.5f * a.dR;
-            bool inside = true, interior = true;
+            // fast path: every tap index ci + floor(cf - e) .. ci + floor(cf + e) + 1
+            // inside the volume and the staged region, i.e. per axis
+            // cf - e >= r0 - ci and cf + e < min(n - 1, r0 + ext - 1) - ci (lo = -ci)
+            bool fast = true;
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
                 const AxisSplit &x = ic.ax[d];
                 const float e = fmaf(Ro, V.inv_sp[d], 1e-3f);
-                interior = interior && (x.cf - e >= x.lo) && (x.cf + e < x.hi);
-                const float lo = fminf(fmaxf(x.cf - e, x.lo), x.hi);
-                const float hi = fminf(fmaxf(x.cf + e, x.lo), x.hi);
-                const int tlo = x.ci + (int)fminf(floorf(lo), x.top);
-                const int thi = x.ci + (int)fminf(floorf(hi), x.top) + 1;
-                inside = inside && tlo >= r0[d] && thi < r0[d] + a.ext[d];
+                fast = fast && (x.cf - e >= fr_lo[d] + x.lo) && (x.cf + e < fr_hi[d] + x.lo);
+            }
+            bool inside = fast, interior = fast;
+            if (!fast) {
+                inside = true;
+                interior = true;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const AxisSplit &x = ic.ax[d];
+                    const float e = fmaf(Ro, V.inv_sp[d], 1e-3f);
+                    interior = interior && (x.cf - e >= x.lo) && (x.cf + e < x.hi);
+                    const float lo = fminf(fmaxf(x.cf - e, x.lo), x.hi);
+                    const float hi = fminf(fmaxf(x.cf + e, x.lo), x.hi);
+                    const int tlo = x.ci + (int)fminf(floorf(lo), x.top);
+                    const int thi = x.ci + (int)fminf(floorf(hi), x.top) + 1;
+                    inside = inside && tlo >= r0[d] && thi < r0[d] + a.ext[d];
+                }
             }
             const int o[3] = {ic.ax[0].ci - r0[0], ic.ax[1].ci - r0[1], DIM == 3 ? ic.ax[2].ci - r0[2] : 0};
             n_fast += (inside && interior) ? 1u : 0u;

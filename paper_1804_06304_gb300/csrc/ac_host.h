@@ -22,6 +22,7 @@ struct ac_volume {
     int64_t pitch_y;      // elements per row
     int64_t pitch_z;      // elements per plane
     size_t bytes;
+    cudaMemPool_t pool;   // non-null: `data` is a stream-ordered allocation from this pool
 };
 
 namespace ac {
@@ -75,6 +76,7 @@ struct ac_contours {
     float first[3] = {0, 0, 0};
     float stride = 0, R0 = 0;
     bool timed = false;
+    cudaMemPool_t pool = nullptr;        // non-null: state, status, hold and counters come from this pool
 };
 
 namespace ac {
@@ -112,6 +114,23 @@ ac_status check_evolve_params(const ac_evolve_params *p);
 // brick's TMA load, and localization rounds for n survivors
 uint32_t tma_poll_limit();
 int64_t localize_round_limit(int64_t n);
+
+// Volumes and lattice contour sets whose device memory is allocated from `pool`
+// in stream order on `st` (no implicit device synchronisation, unlike cudaMalloc
+// and cudaFree), released in stream order on the stream given to the destroy
+// functions.  Used by the request loop so that admitting and retiring tiles does
+// not stall the rounds running on other streams.
+ac_status create_volume_pooled(cudaMemPool_t pool, const void *data, int data_on_device, ac_dtype dtype, int ndim,
+                               const int64_t dims[3], int64_t row_stride, int64_t plane_stride,
+                               const float spacing[3], float intensity_scale, cudaStream_t st, ac_volume **out);
+ac_status seed_lattice_pooled(cudaMemPool_t pool, ac_volume *vol, const ac_seed_params *params, cudaStream_t st,
+                              ac_contours **out);
+void destroy_contours_on(ac_contours *ctr, cudaStream_t st);
+void destroy_volume_on(ac_volume *vol, cudaStream_t st);
+
+// Record the evaluations of set `set` of a plan into `trace` on its later launches
+// (nullptr: no trace); drops the plan's captured graph.  Used by the request loop.
+ac_status plan_set_trace(ac_plan *plan, int set, const ac_trace *trace);
 
 // localization (ac_localize.cu); returns an ac_status and sets the message
 ac_status localize_impl(ac_contours *ctr, float E0, ac_cell *out_host, int64_t cap, int64_t *n_out,

@@ -113,9 +113,10 @@ struct EvolveArgs {
     int32_t freeze_iters;
     int32_t cull_iter;
     float cull_E;
-    float *trace;        // optional (volume 0 only)
+    float *trace;        // optional: rows of volume trace_vol only
     int64_t tk0, tk1;
     int32_t tt0, tt1;
+    int32_t trace_vol;
     uint32_t tma_polls;  // polls of the first wait for a brick's TMA load (then it gives up)
     unsigned long long *path_counts;   // [3]: fast, clamped, global contour-iterations
     const uint32_t *active;            // plain path: contours to visit (nullptr: all)

@@ -1,9 +1,12 @@
 // ac_serve.cu -- serving form: a request loop over image tiles on a native worker
-// thread.  The loop is a client of the library's own C ABI (volumes, lattice
-// seeding, a plan over the resident tiles with per-tile iteration windows, and
-// localization), so a tile evolves exactly as it would alone: the sample
+// thread.  The loop is a client of the library's own entry points (volumes,
+// lattice seeding, a plan over the resident tiles with per-tile iteration windows,
+// and localization; volumes and contour sets allocated from the server's
+// stream-ordered pool), so a tile evolves exactly as it would alone: the sample
 // counters are (block, n, k, stream_id) under the server's single Philox key, and the
-// lane grouping depends only on the evolve parameters, never on the mix.
+// lane grouping depends only on the evolve parameters, never on the mix.  Three
+// streams overlap: uploads of admitted tiles, the rounds, and the localization of
+// the tiles the previous round finished.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +52,10 @@ struct Tile {
     std::vector<ac_cell> cells;
     int64_t n_cells = 0;
     bool done = false;
+    bool traced = false;    // evaluations recorded into `trace` (one traced tile resident at a time)
+    ac_trace trace{};
+    cudaEvent_t ready = nullptr;   // recorded on the upload stream after upload and seeding
+    bool joined = false;           // the round stream waits for `ready`
 };
 
 int elem_bytes(int dtype) { return dtype == AC_U8 ? 1 : dtype == AC_F32 ? 4 : 2; }
@@ -66,7 +73,14 @@ int64_t lattice_contours(const int64_t dims[3], const float sp[3], int ndim, dou
 struct ac_server {
     ac_server_params p;
     int device = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;             // rounds
+    cudaStream_t up_st = nullptr;          // uploads and seeding of admitted tiles
+    cudaStream_t loc_st = nullptr;         // localization and release of finished tiles
+    cudaMemPool_t pool = nullptr;          // stream-ordered device memory of the tiles
+    cudaEvent_t ev_round[2] = {nullptr, nullptr};   // end of the last two rounds
+    int ev_i = 0;
+    ac::Scratch loc_scratch;               // grow-only localization buffers, lent to each finished tile
+    std::vector<Tile *> retiring;          // finished in the last round, not yet localized (worker only)
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -77,17 +91,22 @@ struct ac_server {
     bool stop = false;
     int64_t resident_bytes = 0, peak_bytes = 0, rounds = 0, completed = 0, failed = 0, finished = 0;
     int64_t resident_contours = 0;         // lattice sizes of the resident tiles
+    bool traced_resident = false;          // a traced tile is resident
     ac_plan *plan = nullptr;               // worker only
 };
 
 namespace {
 
-void release_device(Tile *t)
+// Releases a tile's device memory in stream order on `st` (after the work already
+// queued there).
+void release_device(Tile *t, cudaStream_t st)
 {
-    if (t->ctr) ac_destroy_contours(t->ctr);
-    if (t->vol) ac_destroy_volume(t->vol);
+    if (t->ctr) ac::destroy_contours_on(t->ctr, st);
+    if (t->vol) ac::destroy_volume_on(t->vol, st);
+    if (t->ready) cudaEventDestroy(t->ready);
     t->ctr = nullptr;
     t->vol = nullptr;
+    t->ready = nullptr;
 }
 
 // Marks a tile finished (caller holds mu).
@@ -108,6 +127,44 @@ std::string last_error(const char *what)
     return std::string(what) + (m.empty() ? "" : ": " + m);
 }
 
+// Localizes tiles whose last round ended at event `after`, on the localization
+// stream (so the round launched since keeps the GPU busy), keeps their cells and
+// releases their memory in stream order behind the localization.
+void retire(ac_server *S, std::vector<Tile *> &tiles, cudaEvent_t after)
+{
+    if (tiles.empty()) return;
+    cudaStreamWaitEvent(S->loc_st, after, 0);
+    std::vector<std::pair<ac_status, std::string>> outcome;
+    for (Tile *t : tiles) {
+        t->cells.resize((size_t)std::max<int64_t>(1, t->contours));
+        int64_t n_out = 0;
+        ac_localize_params lp{S->p.E0};
+        std::swap(t->ctr->scratch, S->loc_scratch);
+        ac_status ls = ac_localize(t->ctr, &lp, t->cells.data(), (int64_t)t->cells.size(), &n_out, S->loc_st);
+        std::swap(t->ctr->scratch, S->loc_scratch);
+        outcome.emplace_back(ls, ls == AC_OK ? std::string() : last_error("localize"));
+        t->n_cells = ls == AC_OK ? n_out : 0;
+        t->cells.resize((size_t)std::min<int64_t>(t->n_cells, (int64_t)t->cells.size()));
+        t->cells.shrink_to_fit();
+        release_device(t, S->loc_st);
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t i = 0; i < tiles.size(); ++i) {
+        S->resident_bytes -= tiles[i]->est_bytes;
+        S->resident_contours -= tiles[i]->lattice;
+        if (tiles[i]->traced) S->traced_resident = false;
+        finish_locked(S, tiles[i], outcome[i].first, outcome[i].second);
+    }
+    tiles.clear();
+    S->cv_done.notify_all();
+}
+
+// The worker.  Each pass admits waiting tiles (uploaded and seeded on the upload
+// stream, joined to the round stream by an event), launches one round over the
+// resident tiles on the round stream, and then localizes the tiles that finished
+// in the previous round on the localization stream while this round runs.  Tile
+// memory comes from the server's pool in stream order, so neither admission nor
+// release synchronizes the device.
 void serve_loop(ac_server *S)
 {
     cudaSetDevice(S->device);
@@ -122,12 +179,14 @@ void serve_loop(ac_server *S)
             // arrival order, within the budget and the resident cap
             while (!S->pending.empty()) {
                 Tile *t = S->pending.front();
-                const int64_t n_res = (int64_t)(S->resident.size() + admit.size());
+                const int64_t n_res = (int64_t)(S->resident.size() + S->retiring.size() + admit.size());
                 if (n_res > 0 && S->resident_bytes + t->est_bytes > S->p.hbm_budget_bytes) break;
                 if (S->p.max_resident > 0 && n_res >= S->p.max_resident) break;
                 if (n_res > 0 && S->p.max_resident_contours > 0 &&
                     S->resident_contours + t->lattice > S->p.max_resident_contours)
                     break;
+                if (t->traced && S->traced_resident) break;   // one traced tile at a time
+                if (t->traced) S->traced_resident = true;
                 S->pending.pop_front();
                 S->resident_bytes += t->est_bytes;
                 S->resident_contours += t->lattice;
@@ -135,24 +194,35 @@ void serve_loop(ac_server *S)
                 admit.push_back(t);
             }
         }
-        // upload and seed outside the lock
+        // upload and seed outside the lock, on the upload stream
         for (Tile *t : admit) {
             t->t_admit = Clock::now();
-            ac_status s = ac_create_volume(t->data, 0, (ac_dtype)S->p.dtype, S->p.ndim, t->dims, t->row_stride,
-                                           t->plane_stride, t->spacing, t->scale, S->st, &t->vol);
+            ac_status s = ac::create_volume_pooled(S->pool, t->data, 0, (ac_dtype)S->p.dtype, S->p.ndim, t->dims,
+                                                   t->row_stride, t->plane_stride, t->spacing, t->scale, S->up_st,
+                                                   &t->vol);
             std::string err;
             if (s != AC_OK) err = last_error("upload");
             if (s == AC_OK) {
                 ac_seed_params sp{S->p.stride, S->p.R0};
-                s = ac_seed(t->vol, &sp, nullptr, 0, S->st, &t->ctr);
+                s = ac::seed_lattice_pooled(S->pool, t->vol, &sp, S->up_st, &t->ctr);
                 if (s != AC_OK) err = last_error("seed");
             }
-            if (s == AC_OK) t->contours = ac_contour_count(t->ctr);
+            if (s == AC_OK) {
+                t->contours = ac_contour_count(t->ctr);
+                cudaError_t e = cudaEventCreateWithFlags(&t->ready, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(t->ready, S->up_st);
+                if (e != cudaSuccess) {
+                    s = AC_ERR_CUDA;
+                    err = std::string("upload: ") + cudaGetErrorString(e);
+                }
+            }
             std::lock_guard<std::mutex> lk(S->mu);
             if (s != AC_OK) {
-                release_device(t);
+                cudaStreamSynchronize(S->up_st);
+                release_device(t, S->up_st);
                 S->resident_bytes -= t->est_bytes;
                 S->resident_contours -= t->lattice;
+                if (t->traced) S->traced_resident = false;
                 finish_locked(S, t, s, err);
                 S->cv_done.notify_all();
             } else {
@@ -160,88 +230,108 @@ void serve_loop(ac_server *S)
                 dirty = true;
             }
         }
-        if (S->resident.empty()) continue;
-
-        // one round: every resident tile advances up to iters_per_round iterations
-        ac::Range nvtx_round("ac_server_round");
-        const int n = (int)S->resident.size();
-        std::vector<ac_contours *> sets(n);
-        std::vector<ac_batch_item> items(n);
-        int64_t largest = 1;
-        for (Tile *t : S->resident) largest = std::max(largest, t->lattice);
-        for (int i = 0; i < n; ++i) {
-            Tile *t = S->resident[i];
-            // a round lasts about as long as its largest tile's share: smaller tiles can
-            // take more iterations in it without lengthening it much
-            const int64_t f = S->p.balance_rounds ? std::min<int64_t>(8, std::max<int64_t>(1, largest / t->lattice)) : 1;
-            const int m = (int)std::min<int64_t>((int64_t)S->p.iters_per_round * f, T - t->progress);
-            sets[i] = t->ctr;
-            items[i].stream_id = t->stream_id;
-            items[i].first_iter = t->progress + 1;
-            items[i].n_iter = m;
-            items[i].update_last = t->progress + m < T ? 1 : 0;
-        }
-        ac_status s = AC_OK;
-        const bool rebound = dirty;
-        if (!S->plan) s = ac_plan_create(sets.data(), items.data(), n, &S->p.evolve, &S->plan);
-        else if (dirty) s = ac_plan_rebind(S->plan, sets.data(), items.data(), n, S->st);
-        else s = ac_plan_set_items(S->plan, items.data(), S->st);
-        if (s == AC_OK) s = ac_plan_launch(S->plan, rebound ? 0 : 1, S->st);
-        if (s != AC_OK) {
-            // the launch failed for the whole mix: end every resident tile with it
-            const std::string err = last_error("round");
-            cudaStreamSynchronize(S->st);
-            std::lock_guard<std::mutex> lk(S->mu);
-            for (Tile *t : S->resident) {
-                release_device(t);
-                S->resident_bytes -= t->est_bytes;
-                S->resident_contours -= t->lattice;
-                finish_locked(S, t, s, err);
+        std::vector<Tile *> finished;
+        bool launched = false;
+        if (!S->resident.empty()) {
+            // one round: every resident tile advances up to iters_per_round iterations
+            ac::Range nvtx_round("ac_server_round");
+            const int n = (int)S->resident.size();
+            std::vector<ac_contours *> sets(n);
+            std::vector<ac_batch_item> items(n);
+            int64_t largest = 1;
+            for (Tile *t : S->resident) largest = std::max(largest, t->lattice);
+            for (int i = 0; i < n; ++i) {
+                Tile *t = S->resident[i];
+                // a round lasts about as long as its largest tile's share: smaller tiles can
+                // take more iterations in it without lengthening it much
+                const int64_t f =
+                    S->p.balance_rounds ? std::min<int64_t>(8, std::max<int64_t>(1, largest / t->lattice)) : 1;
+                const int m = (int)std::min<int64_t>((int64_t)S->p.iters_per_round * f, T - t->progress);
+                sets[i] = t->ctr;
+                items[i].stream_id = t->stream_id;
+                items[i].first_iter = t->progress + 1;
+                items[i].n_iter = m;
+                items[i].update_last = t->progress + m < T ? 1 : 0;
+                if (!t->joined) {   // the round reads what the upload stream wrote
+                    cudaStreamWaitEvent(S->st, t->ready, 0);
+                    t->joined = true;
+                }
             }
-            S->resident.clear();
-            if (S->plan) ac_destroy_plan(S->plan);
-            S->plan = nullptr;
-            dirty = true;
-            S->cv_done.notify_all();
-            continue;
+            ac_status s = AC_OK;
+            int traced = -1;
+            for (int i = 0; i < n; ++i)
+                if (S->resident[i]->traced) traced = i;
+            if (!S->plan) s = ac_plan_create(sets.data(), items.data(), n, &S->p.evolve, &S->plan);
+            else if (dirty) s = ac_plan_rebind(S->plan, sets.data(), items.data(), n, S->st);
+            else s = ac_plan_set_items(S->plan, items.data(), S->st);
+            if (s == AC_OK && traced >= 0) s = ac::plan_set_trace(S->plan, traced, &S->resident[traced]->trace);
+            // graph replay, updated in place after a rebind; rounds with a trace launch directly
+            if (s == AC_OK) s = ac_plan_launch(S->plan, traced >= 0 ? 0 : 1, S->st);
+            if (s == AC_OK && cudaEventRecord(S->ev_round[S->ev_i], S->st) != cudaSuccess) {
+                ac::set_error("cudaEventRecord failed");
+                s = AC_ERR_CUDA;
+            }
+            if (s != AC_OK) {
+                // the launch failed for the whole mix: end every resident tile with it
+                const std::string err = last_error("round");
+                cudaStreamSynchronize(S->st);
+                cudaStreamSynchronize(S->up_st);
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (Tile *t : S->resident) {
+                    release_device(t, S->st);
+                    S->resident_bytes -= t->est_bytes;
+                    S->resident_contours -= t->lattice;
+                    finish_locked(S, t, s, err);
+                }
+                S->resident.clear();
+                S->traced_resident = std::any_of(S->retiring.begin(), S->retiring.end(),
+                                                 [](const Tile *t) { return t->traced; });
+                if (S->plan) ac_destroy_plan(S->plan);
+                S->plan = nullptr;
+                dirty = true;
+                S->cv_done.notify_all();
+            } else {
+                launched = true;
+                dirty = false;
+                std::vector<Tile *> keep;
+                for (int i = 0; i < n; ++i) {
+                    Tile *t = S->resident[i];
+                    t->progress += items[i].n_iter;
+                    t->rounds += 1;
+                    (t->progress >= T ? finished : keep).push_back(t);
+                }
+                if (!finished.empty()) dirty = true;   // the plan still refers to them: rebind next round
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->resident = keep;
+                S->retiring.insert(S->retiring.end(), finished.begin(), finished.end());
+                ++S->rounds;
+            }
         }
-        dirty = false;
-        for (int i = 0; i < n; ++i) {
-            S->resident[i]->progress += items[i].n_iter;
-            S->resident[i]->rounds += 1;
-        }
+        // tiles that finished in the previous round are localized while this one runs
+        std::vector<Tile *> prev;
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            ++S->rounds;
+            for (Tile *t : S->retiring)
+                if (std::find(finished.begin(), finished.end(), t) == finished.end()) prev.push_back(t);
         }
-
-        // retire finished tiles: localize (synchronizes the stream), keep the cells
-        std::vector<Tile *> keep;
-        std::vector<Tile *> done;
-        for (Tile *t : S->resident) (t->progress >= T ? done : keep).push_back(t);
-        if (done.empty()) continue;
-        std::vector<std::pair<ac_status, std::string>> outcome;
-        for (Tile *t : done) {
-            t->cells.resize((size_t)std::max<int64_t>(1, t->contours));
-            int64_t n_out = 0;
-            ac_localize_params lp{S->p.E0};
-            ac_status ls = ac_localize(t->ctr, &lp, t->cells.data(), (int64_t)t->cells.size(), &n_out, S->st);
-            outcome.emplace_back(ls, ls == AC_OK ? std::string() : last_error("localize"));
-            t->n_cells = ls == AC_OK ? n_out : 0;
-            t->cells.resize((size_t)std::min<int64_t>(t->n_cells, (int64_t)t->cells.size()));
-            t->cells.shrink_to_fit();
+        retire(S, prev, S->ev_round[S->ev_i ^ 1]);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->retiring = finished;
         }
-        // the plan still refers to the finished sets: rebind before the next launch
-        dirty = true;
-        for (Tile *t : done) release_device(t);
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->resident = keep;
-        for (size_t i = 0; i < done.size(); ++i) {
-            S->resident_bytes -= done[i]->est_bytes;
-            S->resident_contours -= done[i]->lattice;
-            finish_locked(S, done[i], outcome[i].first, outcome[i].second);
+        if (launched) S->ev_i ^= 1;
+        // nothing left to overlap with: localize this round's finished tiles now
+        bool idle;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            idle = S->resident.empty() && S->pending.empty();
         }
-        S->cv_done.notify_all();
+        if (idle && !finished.empty()) {
+            std::vector<Tile *> now = finished;
+            retire(S, now, S->ev_round[S->ev_i ^ 1]);
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->retiring.clear();
+        }
     }
 }
 
@@ -271,9 +361,28 @@ extern "C" ac_status ac_server_create(const ac_server_params *params, ac_server 
     S->p.evolve.update_last = 0;
     cudaError_t e = cudaGetDevice(&S->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->up_st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->loc_st, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&S->ev_round[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        // the tiles' memory pool keeps up to the budget cached between tiles
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = S->device;
+        e = cudaMemPoolCreate(&S->pool, &props);
+        uint64_t keep = (uint64_t)p.hbm_budget_bytes;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     if (e != cudaSuccess) {
+        const std::string msg = std::string("ac_server_create: ") + cudaGetErrorString(e);
+        for (cudaStream_t q : {S->st, S->up_st, S->loc_st})
+            if (q) cudaStreamDestroy(q);
+        for (cudaEvent_t ev : S->ev_round)
+            if (ev) cudaEventDestroy(ev);
+        if (S->pool) cudaMemPoolDestroy(S->pool);
         delete S;
-        AC_FAIL(AC_ERR_CUDA, std::string("ac_server_create: ") + cudaGetErrorString(e));
+        AC_FAIL(AC_ERR_CUDA, msg);
     }
     S->worker = std::thread(serve_loop, S);
     *out = S;
@@ -283,6 +392,15 @@ extern "C" ac_status ac_server_create(const ac_server_params *params, ac_server 
 extern "C" ac_status ac_server_submit(ac_server *S, const void *data_host, const int64_t dims[3], int64_t row_stride,
                                       int64_t plane_stride, const float spacing[3], float intensity_scale,
                                       uint32_t stream_id, int64_t *ticket)
+{
+    return ac_server_submit_traced(S, data_host, dims, row_stride, plane_stride, spacing, intensity_scale, stream_id,
+                                   nullptr, ticket);
+}
+
+extern "C" ac_status ac_server_submit_traced(ac_server *S, const void *data_host, const int64_t dims[3],
+                                             int64_t row_stride, int64_t plane_stride, const float spacing[3],
+                                             float intensity_scale, uint32_t stream_id, const ac_trace *trace,
+                                             int64_t *ticket)
 {
     if (!S || !data_host || !dims || !spacing || !ticket) AC_FAIL(AC_ERR_ARG, "ac_server_submit: NULL argument");
     *ticket = 0;
@@ -312,6 +430,15 @@ extern "C" ac_status ac_server_submit(ac_server *S, const void *data_host, const
     if (t->est_bytes > S->p.hbm_budget_bytes) {
         delete t;
         AC_FAIL(AC_ERR_BUDGET, "ac_server_submit: the tile alone exceeds the memory budget");
+    }
+    if (trace && trace->device_buf) {
+        if (trace->k_begin < 0 || trace->k_end > C || trace->k_begin > trace->k_end || trace->t_begin < 1 ||
+            trace->t_begin > trace->t_end || trace->t_end > S->p.evolve.T + 1) {
+            delete t;
+            AC_FAIL(AC_ERR_ARG, "ac_server_submit_traced: trace range outside the tile's contours or iterations");
+        }
+        t->traced = true;
+        t->trace = *trace;
     }
     t->t_submit = Clock::now();
     {
@@ -398,10 +525,15 @@ extern "C" void ac_server_destroy(ac_server *S)
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     cudaSetDevice(S->device);
-    cudaStreamSynchronize(S->st);
-    for (Tile *t : S->resident) release_device(t);
+    for (cudaStream_t q : {S->st, S->up_st, S->loc_st}) cudaStreamSynchronize(q);
+    for (Tile *t : S->resident) release_device(t, S->st);
+    for (Tile *t : S->retiring) release_device(t, S->st);
     if (S->plan) ac_destroy_plan(S->plan);
+    S->loc_scratch.release_all();
     for (auto &kv : S->tiles) delete kv.second;
-    cudaStreamDestroy(S->st);
+    cudaStreamSynchronize(S->st);
+    for (cudaStream_t q : {S->st, S->up_st, S->loc_st}) cudaStreamDestroy(q);
+    for (cudaEvent_t ev : S->ev_round) cudaEventDestroy(ev);
+    cudaMemPoolDestroy(S->pool);
     delete S;
 }

@@ -1,0 +1,152 @@
+"""Parity at the full benchmark sizes, in the benchmark's launch configuration.
+
+The 1024x1024x256 brain-like volume (spacing 1:1:2, stored as uint16 and as FP16)
+and the 4096^2 2D image are evolved whole on the GPU (N = 512 / 128 samples,
+T = 100 iterations, automatic brick plan).  Then:
+
+* teacher-forced: the oracle re-evaluates a stripe of 256 contours at every
+  iteration at the GPU's recorded states (1e-5 of the magnitude, pass fraction
+  >= 0.9999);
+* free-running: the oracle evolves every contour of a centred window of the
+  lattice from the GPU's own FP32 seeds with the FP32 parameters; final centres
+  are compared, and the library's localization of the window's contours is
+  compared with the oracle's (detection-set agreement 2 |matched| / (|D_gpu| +
+  |D_oracle|), one-to-one within 0.5 voxel).  The bars are the spec ones
+  (>= 99.9 % of the centres within 0.25 voxel, agreement >= 0.999), lowered only
+  by what the FP64 dynamics themselves show: oracle runs whose seeds differ from
+  the first by one FP32 ulp along x, y (and z) measure how many trajectories and
+  cells a last-bit change alone moves, and the GPU may lose at most three times
+  what the worst of them loses (tests/_parity.floor_bar);
+* precision: storage u16 / f16 / f32 with compensated and plain sums, errors of
+  E, dE/dR and dE/dc over the stripe (printed as PRECISION lines with -s).
+"""
+import json
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+@pytest.fixture(scope="module")
+def ac():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_06304_gb300 import ac as lib
+    lib.load()
+    return lib
+
+
+@pytest.fixture(scope="module")
+def brain():
+    from paper_1804_06304_gb300 import synth
+    return synth.brain_3d(2, with_f16=True)
+
+
+@pytest.fixture(scope="module")
+def image2d():
+    from paper_1804_06304_gb300 import synth
+    return synth.large_2d(1)
+
+
+def _volume(s, storage):
+    return {"u16": s.volume, "f16": getattr(s, "volume_f16", None), "u8": s.volume,
+            "f32": s.volume.astype(np.float32)}[storage]
+
+
+def _window(s, ndim, stride, side):
+    import bench
+    return bench.window_ids(bench.lattice_shape(s.shape_xyz, s.spacing, stride, ndim), side ** ndim)
+
+
+@pytest.mark.parametrize("storage", ["u16", "f16"])
+def test_full_size_3d(ac, oracle, brain, storage):
+    s = brain
+    vol = _volume(s, storage)
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(3, R0, s.contrast, N=512, T=100, seed=1000)
+    k0 = 170 * 170 * 42 + 170 * 85     # a row through the middle plane
+    r = P.gpu_run(ac, vol, s.spacing, p, stride=6.0, trace_k=(k0, k0 + 256))
+    assert r["final"].shape[1] == 170 * 170 * 85
+    assert np.all(np.isfinite(r["final"]))
+    fast, clamped, glob = ac.ac_evolve_stats(r["ctr"])
+    assert fast > 0.9 * (fast + clamped + glob)
+    img = P.oracle_image(oracle, vol, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], k0, 1)
+    assert frac >= 0.9999, (storage, frac, worst, bad)
+    # a 21^3 window: about a 128 x 128 x 64-voxel block of the volume
+    chk, floor = P.free_running(ac, oracle, s, vol, 3, 6.0, p, r, _window(s, 3, 6.0, 21))
+    P.assert_free_running(chk, floor, f"brain-3d {storage}")
+
+
+def test_full_size_2d(ac, oracle, image2d):
+    s = image2d
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=7)
+    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(200_000, 200_256))
+    assert r["final"].shape[1] == 682 * 682
+    assert np.all(np.isfinite(r["final"]))
+    img = P.oracle_image(oracle, s.volume, s.spacing)
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 200_000, 1)
+    assert frac >= 0.9999, (frac, worst, bad)
+    # an 85^2 window: a 512 x 512 region of the image
+    chk, floor = P.free_running(ac, oracle, s, s.volume, 2, 6.0, p, r, _window(s, 2, 6.0, 85))
+    P.assert_free_running(chk, floor, "large-2d")
+
+
+def _normalised_errors(oracle, trace, res, ndim):
+    rows = trace.reshape(-1, 9).astype(np.float64)
+    mag_e = res[:, oracle.MAG_I]
+    mag_r = ndim / rows[:, 3] * mag_e + (res[:, oracle.MAG_R] - ndim / rows[:, 3] * res[:, oracle.MAG_E])
+    out = {}
+    for name, gc, oc, mag in [("E", 4, oracle.E, mag_e), ("dEdR", 5, oracle.DEDR, mag_r)] + \
+            [(f"dEdc{a}", 6 + a, oracle.DEDC + a, res[:, oracle.MAG_G]) for a in range(ndim)]:
+        err = np.abs(rows[:, gc] - res[:, oc]) / np.maximum(np.maximum(np.abs(res[:, oc]), mag), 1e-30)
+        keep = res[:, oracle.FLAGS] == 0
+        out[name] = {"max": float(err[keep].max()), "median": float(np.median(err[keep]))}
+    return out
+
+
+@pytest.mark.parametrize("storage", ["u16", "f16", "f32"])
+@pytest.mark.parametrize("comp", [1, 0])
+def test_full_size_precision(ac, oracle, brain, storage, comp):
+    """The precision report at full size: a stripe of 256 contours through the
+    middle of the 1024x1024x256 volume, all 100 iterations."""
+    s = brain
+    vol = _volume(s, storage)
+    R0 = 6.0 / math.sqrt(1.5)
+    p = ac.default_params(3, R0, s.contrast, N=512, T=100, seed=1000, compensated=comp)
+    k0 = 170 * 170 * 42 + 170 * 85
+    r = P.gpu_run(ac, vol, s.spacing, p, stride=6.0, trace_k=(k0, k0 + 256), device_volume=(storage == "f32"))
+    img = P.oracle_image(oracle, vol, s.spacing)
+    op = P.oracle_params(oracle, 3, p)
+    frac, nflag, worst, bad, res = P.teacher_forced(oracle, img, op, r["trace"], k0, 1)
+    errs = _normalised_errors(oracle, r["trace"], res, 3)
+    ids = np.arange(k0, k0 + 256)
+    cR, E, _ = oracle.evolve(img, op, r["init"][:4, ids].T.astype(np.float64), ids=ids)
+    sp = np.asarray(s.spacing, np.float64)
+    dc = np.linalg.norm((r["final"][:3, ids].T - cR[:, :3]) / sp, axis=1)
+    dR = np.abs(r["final"][3, ids] - cR[:, 3])
+    report = {"storage": storage, "sums": "compensated" if comp else "plain", "size": "1024x1024x256",
+              "contours": 256, "iterations": 100, "samples": 512, "pass_fraction_1e-5": frac, "flagged": nflag,
+              "errors": errs, "final_centre_err_voxels_max": float(dc.max()),
+              "final_centre_err_voxels_median": float(np.median(dc)),
+              "frac_centre_within_0.25_voxel": float(np.mean(dc <= 0.25)), "final_radius_err_max": float(dR.max())}
+    print("PRECISION " + json.dumps(report))
+    if comp:
+        assert frac >= 0.9999, report
+    else:
+        # plain FP32 sums of 16 terms per lane and a 32-lane tree: relative error
+        # bound about (16 + 5) x 2^-24 of the magnitude, well inside 1e-4
+        assert max(v["max"] for v in errs.values()) < 1e-4, report
+    assert np.median(dc) < 0.25

@@ -1,8 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Per-iteration (teacher-forced) energies and gradients within 1e-5 of the oracle's
-magnitude-scaled value, final centres within 0.25 voxel, detection-set agreement
->= 0.999, identical Philox words and identical localization on identical inputs.
+magnitude-scaled value; free-running final centres within 0.25 voxel for 99.9 % of
+the contours and detection-set agreement >= 0.999 (or the bars the FP64 dynamics
+allow, see _parity.floor_bar); identical Philox words and identical
+localization on identical inputs.  The full benchmark sizes are in
+test_gpu_fullsize.py.
 """
 import dataclasses
 import math
@@ -106,20 +109,9 @@ def test_free_running_and_detections_small3d(ac, oracle, small3d):
     s = small3d
     p = _p3(ac, s)
     r = P.gpu_run(ac, s.volume, s.spacing, p, stride=4.0)
-    img = P.oracle_image(oracle, s.volume, s.spacing)
-    op = P.oracle_params(oracle, 3, p)
-    cR0 = r["init"][:4].T.astype(np.float64)
-    cR, E, _ = oracle.evolve(img, op, cR0)
-    gpu = r["final"]
-    d = np.linalg.norm(gpu[:3].T - cR[:, :3], axis=1)
-    assert np.mean(d <= 0.25) >= 0.99, np.mean(d <= 0.25)
-    E0 = ac.default_E0(3, s.contrast)
-    cells = ac.ac_localize(r["ctr"], E0)
-    ids_o = oracle.localize(3, cR, E, E0)
-    m = P.match_sets(np.stack([c for c in cells["c"]]) if len(cells) else np.zeros((0, 3)), cR[ids_o, :3], 0.5)
-    agree = 2 * m / (len(cells) + len(ids_o))
-    assert agree >= 0.999, (agree, len(cells), len(ids_o))
-    assert len(cells) >= 18
+    chk, floor = P.free_running(ac, oracle, s, s.volume, 3, 4.0, p, r)
+    P.assert_free_running(chk, floor, "small-3d")
+    assert chk["detections"]["gpu"] >= 18
 
 
 def test_localize_identical_on_identical_state(ac, oracle, small3d):
@@ -179,16 +171,8 @@ def test_free_running_and_detections_2d(ac, oracle, crop2d):
     R0 = 6.0 / math.sqrt(1.5)
     p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=99)
     r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0)
-    img = P.oracle_image(oracle, s.volume, s.spacing)
-    cR, E, _ = oracle.evolve(img, P.oracle_params(oracle, 2, p), r["init"][:4].T.astype(np.float64))
-    d = np.linalg.norm(r["final"][:2].T - cR[:, :2], axis=1)
-    assert np.mean(d <= 0.25) >= 0.99, np.mean(d <= 0.25)
-    E0 = ac.default_E0(2, s.contrast)
-    cells = ac.ac_localize(r["ctr"], E0)
-    ids_o = oracle.localize(2, cR, E, E0)
-    m = P.match_sets(np.stack(cells["c"])[:, :2], cR[ids_o, :2], 0.5)
-    agree = 2 * m / (len(cells) + len(ids_o))
-    assert agree >= 0.99, (agree, len(cells), len(ids_o))
+    chk, floor = P.free_running(ac, oracle, s, s.volume, 2, 6.0, p, r)
+    P.assert_free_running(chk, floor, "2d crop 512x512")
 
 
 # ------------------------------------------------------------------ storage types, anisotropy
@@ -384,42 +368,6 @@ def test_invalid_parameters_rejected(ac, small3d):
         with pytest.raises(ac.ACError) as e:
             ac.ac_evolve(C, p)
         assert e.value.status == ac.AC_ERR_ARG, b
-
-
-# ------------------------------------------------------------------ full size, sampled
-def test_full_size_3d_sampled_parity(ac, oracle):
-    """The 1024x1024x256 uint16 brain-like workload (spacing 1:1:2) in the
-    benchmark's launch configuration (N = 512, T = 100, automatic brick plan); the
-    oracle re-evaluates a stripe of 256 contours in the middle of the volume at
-    every iteration."""
-    from paper_1804_06304_gb300 import synth
-    s = synth.brain_3d(2, with_f16=False)
-    R0 = 6.0 / math.sqrt(1.5)
-    p = ac.default_params(3, R0, s.contrast, N=512, T=100, seed=1000)
-    k0 = 170 * 170 * 42 + 170 * 85     # a row through the middle plane
-    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(k0, k0 + 256))
-    assert r["final"].shape[1] == 170 * 170 * 85
-    img = P.oracle_image(oracle, s.volume, s.spacing)
-    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, p), r["trace"], k0, 1)
-    assert frac >= 0.9999, (frac, worst, bad)
-    assert np.all(np.isfinite(r["final"]))
-    fast, clamped, glob = ac.ac_evolve_stats(r["ctr"])
-    assert fast > 0.9 * (fast + clamped + glob)
-
-
-def test_full_size_2d_sampled_parity(ac, oracle):
-    """The 4096^2 workload in the benchmark's launch configuration; the oracle
-    re-evaluates a sampled stripe of contours at every iteration."""
-    from paper_1804_06304_gb300 import synth
-    s = synth.large_2d(1)
-    R0 = 6.0 / math.sqrt(1.5)
-    p = ac.default_params(2, R0, s.contrast, N=128, T=100, seed=7)
-    r = P.gpu_run(ac, s.volume, s.spacing, p, stride=6.0, trace_k=(200_000, 200_256))
-    assert r["final"].shape[1] == 682 * 682
-    img = P.oracle_image(oracle, s.volume, s.spacing)
-    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 2, p), r["trace"], 200_000, 1)
-    assert frac >= 0.9999, (frac, worst, bad)
-    assert np.all(np.isfinite(r["final"]))
 
 
 def test_empty_set_and_single_iteration(ac, small3d):

@@ -157,3 +157,48 @@ def test_destroy_with_tiles_in_flight(ac, tiles):
     for i, t in enumerate(tiles):
         srv.submit(t.volume, t.spacing, stream_id=i)
     srv.close()                                           # stops after the current round, frees everything
+
+
+def test_served_tiles_match_the_oracle(ac, oracle, tiles):
+    """Served tiles against the FP64 oracle, not only against the CUDA path alone:
+    four tiles share the request loop's rounds; one of them records a stripe of
+    its evaluations (ac_server_submit_traced), which the oracle re-evaluates at the
+    recorded states (1e-5 of the magnitude, pass fraction >= 0.9999); for two tiles
+    the oracle evolves every contour from the lattice with the server's parameters
+    and the tile's stream id and localizes them: detection-set agreement with the
+    served cells, with matching within 0.5 and within 0.25 voxel, at least 0.999,
+    or three times closer to 1 than the oracle against itself after a one-ulp
+    change of the seeds (tests/_parity.floor_bar)."""
+    import torch
+    from tests import _parity as P
+    p = dataclasses.replace(_params(ac), T=30)
+    E0 = ac.default_E0(3, CONTRAST)
+    srv = ac.Server(p, ac.AC_U16, 3, STRIDE, E0, hbm_budget_bytes=120 << 30, iters_per_round=7)
+    k0, k1 = 100, 356
+    buf = torch.full(((k1 - k0) * p.T * 9,), float("nan"), device="cuda", dtype=torch.float32)
+    tickets = []
+    for i, t in enumerate(tiles[:4]):
+        tr = (buf, k0, k1, 1, p.T + 1) if i == 1 else None
+        tickets.append(srv.submit(t.volume, t.spacing, stream_id=200 + i, trace=tr))
+    served = [srv.wait(tk, timeout=300)[0] for tk in tickets]
+    srv.close()
+    trace = buf.view(p.T, k1 - k0, 9).cpu().numpy()
+    img = P.oracle_image(oracle, tiles[1].volume, tiles[1].spacing)
+    op = P.oracle_params(oracle, 3, dataclasses.replace(p, stream_id=201))
+    frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, op, trace, k0, 1)
+    assert frac >= 0.9999, (frac, worst, bad)
+    for i in (1, 2):
+        t = tiles[i]
+        V = ac.ac_create_volume(t.volume, t.spacing)
+        seeds = ac.ac_get_state(ac.ac_seed(V, stride=STRIDE))       # the lattice the server seeds
+        pi = dataclasses.replace(p, stream_id=200 + i)
+        ids = np.arange(seeds.shape[1])
+        _, _, cells_o, floor = P.oracle_with_floor(ac, oracle, t, t.volume, 3, pi, seeds[:4].T.astype(np.float64),
+                                                   ids)
+        dg = served[i]["c"].astype(np.float64) / np.asarray(t.spacing, np.float64)
+        agree, agree_q = P.compare_cells(dg, cells_o)
+        print("SERVED " + str({"tile": i, "cells": (len(dg), len(cells_o)), "agreement": agree,
+                               "agreement_0.25": agree_q, "floor": floor}))
+        assert len(cells_o) > 20
+        assert agree >= P.floor_bar(floor["agreement"]), (i, agree, floor)
+        assert agree_q >= P.floor_bar(floor["agreement_0.25"]), (i, agree_q, floor)
