@@ -736,7 +736,8 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
             // fast path: every tap index ci + floor(cf - e) .. ci + floor(cf + e) + 1
             // inside the volume and the staged region, i.e. per axis
             // cf - e >= r0 - ci and cf + e < min(n - 1, r0 + ext - 1) - ci (lo = -ci)
-            bool fast = true;
+            // (3D; in 2D the full test below is as cheap)
+            bool fast = DIM == 3;
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
                 const AxisSplit &x = ic.ax[d];
