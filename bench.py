@@ -47,10 +47,13 @@ import numpy as np  # noqa: E402
 # per block of B samples), with each pair of independent FP32 operations that the
 # packed two-lane instructions can take counted as one slot.  2D: 52.75 (a Philox
 # block serves two samples; one quad load of row values and x-differences per
-# bilinear gather; B = 8); 3D: 102.25 (three blocks per four samples; eight
-# 8/16-bit taps, each one operation from exact biased floats; B = 4).  The
-# per-iteration reduction and update are excluded.
+# bilinear gather; B = 8); 3D: 102.25 (counted when a 3D sample took three whole
+# words; eight 8/16-bit taps, each one operation from exact biased floats; B = 4).
+# The per-iteration reduction and update are excluded.  These counts are frozen as
+# the definition of the work; the two-word 3D samples of the current kernel (one
+# block per two samples) have a leaner count of their own, 95.25, reported beside.
 ALG_SLOTS_PER_SAMPLE = {2: 52.75, 3: 102.25}
+ALG_SLOTS_CURRENT = {2: 52.75, 3: 95.25}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
 # ncu capture of the current kernel (to be removed when the kernel changes), scaled
 # with the volume and contour count: the 2048^2 instance of large-2d read 7.03 MB
@@ -528,10 +531,12 @@ def main(argv=None):
     peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
     traffic = DRAM_BYTES_PER_LAUNCH.get((args.workload, args.path, args.size, args.dtype))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s", "frac": achieved / peak,
+            "frac_current_formulation": ALG_SLOTS_CURRENT[ndim] * samples / (k_ms * 1e-3) / 1e12 / peak,
             "traffic": traffic,
             "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: ncu capture of a "
                             "smaller instance (2048^2 / 256x256x64) scaled with the volume", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
             "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
+            "alg_slots_per_sample_current": ALG_SLOTS_CURRENT[ndim],
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
 
     # the other roofs the path touches: HBM (the volume and the contour state per

@@ -121,10 +121,11 @@ ac_status ac_reseed(ac_contours *ctr, void *cuda_stream);
  * ac_evolve -- T iterations of Monte-Carlo gradient descent for every contour
  * (stages a3-a8).  Iteration n, for contour k at centre c and radius R:
  *   samples  x_j = c + (R + dR/2) u_j, j < N, u_j uniform in the unit ball (disk)
- *            from the words d j .. d j + d - 1 of the stream Philox4x32-10(counter
- *            = (b, n, k, stream_id), key = (seed low 32 bits, seed high 32 bits)),
- *            b = 0, 1, ..., four words per block (2D: one block per two samples,
- *            3D: three blocks per four) -- "Monte-Carlo Integration" section;
+ *            from the words 2j and 2j + 1 of the stream Philox4x32-10(counter =
+ *            (b, n, k, stream_id), key = (seed low 32 bits, seed high 32 bits)),
+ *            b = 0, 1, ..., four words per block, one block per two samples (2D:
+ *            one 24-bit uniform per word; 3D: three 21-bit uniforms from the two
+ *            words) -- "Monte-Carlo Integration" section;
  *   sums     J = V/N sum S I, J_R = V/N sum dS/dR I, J_c = V/N sum S'(r)(-(x-c)/r) I
  *            with V the volume (area) of the ball and S the four-region weight of
  *            Eq. 5 (linear bands of widths dR and dR / 2^(1/d));

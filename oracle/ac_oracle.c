@@ -36,11 +36,13 @@
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
  *     (block, iteration, contour, stream) and key (seed_lo, seed_hi); the words of
  *     one iteration and contour form the stream block 0, block 1, ... (four words
- *     each) and sample j takes words d j .. d j + d - 1 (2D: one block per two
- *     samples; 3D: three blocks per four samples); a uniform is (w >> 8) * 2^-24;
- *     3D ball point = cbrt(u0) (sin phi cos th, sin phi sin th, cos phi) with
- *     cos phi = 1 - 2 u1, th = 2 pi u2; 2D disk point follows the paper's
- *     (sqrt(u0) cos th, sqrt(u0) sin th), th = 2 pi u1;
+ *     each) and sample j takes words 2 j and 2 j + 1 (one block per two samples);
+ *     2D: two 24-bit uniforms u = (w >> 8) * 2^-24, one per word, and the paper's
+ *     disk point (sqrt(u0) cos th, sqrt(u0) sin th), th = 2 pi u1; 3D: three 21-bit
+ *     uniforms from the 64 bits, u0 = the top 21 bits of w0, u1 = the low 21 bits of
+ *     w1, u2 = the low 11 bits of w0 followed by the top 10 bits of w1, each times
+ *     2^-21, and the ball point cbrt(u0) (sin phi cos th, sin phi sin th, cos phi)
+ *     with cos phi = 1 - 2 u1, th = 2 pi u2;
  *   - clamps that the paper does not state: |dc| <= max_step, |dR| <= max_step,
  *     R in [Rmin, Rmax], c inside the box of voxel centres;
  *   - T iterations = T evaluations; the update follows evaluations 1..T-1, so the
@@ -87,16 +89,29 @@ double or_uniform24(uint32_t w)
     return (double)(w >> 8) * (1.0 / 16777216.0);
 }
 
-/* Uniform point in the unit ball (ndim 3) or unit disk (ndim 2).  For the disk,
- * `which` selects the first (words 0,1) or second (words 2,3) sample of the block. */
-/* The unit-ball (disk) point of one sample from its ndim random words. */
-void or_unit_sample(int ndim, const uint32_t w[3], double u[3])
+/* The three 21-bit uniforms of a 3D sample from its two words: the 64 bits give
+ * u0 = w0 bits 31..11, u1 = w1 bits 20..0, u2 = w0 bits 10..0 then w1 bits 31..22,
+ * each an integer below 2^21 times 2^-21 (w1 bit 21 is unused). */
+void or_uniforms21(uint32_t w0, uint32_t w1, double u[3])
+{
+    const uint32_t a = w0 >> 11;
+    const uint32_t b = w1 & 0x1FFFFFu;
+    const uint32_t c = ((w0 & 0x7FFu) << 10) | (w1 >> 22);
+    u[0] = (double)a / 2097152.0;
+    u[1] = (double)b / 2097152.0;
+    u[2] = (double)c / 2097152.0;
+}
+
+/* The unit-ball (disk) point of one sample from its two random words. */
+void or_unit_sample(int ndim, const uint32_t w[2], double u[3])
 {
     if (ndim == 3) {
-        double rad = cbrt(or_uniform24(w[0]));
-        double cphi = 1.0 - 2.0 * or_uniform24(w[1]);
+        double v[3];
+        or_uniforms21(w[0], w[1], v);
+        double rad = cbrt(v[0]);
+        double cphi = 1.0 - 2.0 * v[1];
         double sphi = sqrt(fmax(0.0, 1.0 - cphi * cphi));
-        double th = 2.0 * OR_PI * or_uniform24(w[2]);
+        double th = 2.0 * OR_PI * v[2];
         u[0] = rad * sphi * cos(th);
         u[1] = rad * sphi * sin(th);
         u[2] = rad * cphi;
@@ -270,10 +285,10 @@ typedef struct {
     uint32_t w[4];
 } word_stream;
 
-static void sample_words(const or_params *P, word_stream *S, int64_t j, int64_t iter, int64_t k, uint32_t out[3])
+static void sample_words(const or_params *P, word_stream *S, int64_t j, int64_t iter, int64_t k, uint32_t out[2])
 {
-    for (int t = 0; t < P->ndim; ++t) {
-        const int64_t m = (int64_t)P->ndim * j + t;
+    for (int t = 0; t < 2; ++t) {
+        const int64_t m = 2 * j + t;
         if (m / 4 != S->blk) {
             S->blk = m / 4;
             sample_block(P, S->blk, iter, k, S->w);
@@ -394,7 +409,7 @@ void or_eval_pq(const or_image *img, const or_params *P, const double p[3], cons
     or_sums A;
     memset(&A, 0, sizeof(A));
     word_stream S = {-1, {0, 0, 0, 0}};
-    uint32_t w[3];
+    uint32_t w[2];
     for (int64_t j = 0; j < P->N; ++j) {
         double u[3], x[3];
         sample_words(P, &S, j, iter, k, w);
@@ -704,7 +719,7 @@ void or_image_values(const or_image *img, int64_t n, const double *x, double *ou
 void or_unit_samples(const or_params *P, int64_t iter, int64_t k, double *out)
 {
     word_stream S = {-1, {0, 0, 0, 0}};
-    uint32_t w[3];
+    uint32_t w[2];
     for (int64_t j = 0; j < P->N; ++j) {
         sample_words(P, &S, j, iter, k, w);
         or_unit_sample(P->ndim, w, out + 3 * j);

@@ -79,6 +79,7 @@ def lib():
                 "or_philox4x32_10": (None, [U32, U32, U32]),
                 "or_philox_batch": (None, [ct.c_int64, U32, U32, U32]),
                 "or_uniform24": (ct.c_double, [ct.c_uint32]),
+                "or_uniforms21": (None, [ct.c_uint32, ct.c_uint32, D]),
                 "or_half_to_double": (ct.c_double, [ct.c_uint16]),
                 "or_image_value": (ct.c_double, [IP, D]),
                 "or_image_values": (None, [IP, ct.c_int64, D, D]),
@@ -175,6 +176,13 @@ def philox(ctrs: np.ndarray, key) -> np.ndarray:
 
 def uniform24(w: int) -> float:
     return lib().or_uniform24(int(w))
+
+
+def uniforms21(w0: int, w1: int):
+    """The three 21-bit uniforms a 3D sample draws from its two words."""
+    out = np.empty(3)
+    lib().or_uniforms21(int(w0), int(w1), _P(out, ct.c_double))
+    return tuple(out)
 
 
 def half_to_double(bits: int) -> float:

@@ -370,38 +370,47 @@ __device__ __forceinline__ void add_terms4(Acc &acc, const Terms &x, const Terms
 
 // All samples of one contour-iteration handled by this lane (lane `lig` of G).
 // The words of iteration n of contour k form the stream Philox(0, n, k, stream),
-// Philox(1, n, k, stream), ... (four words per block) and sample j takes words
-// d j .. d j + d - 1.  3D: the quad of samples 4q .. 4q + 3 takes blocks 3q,
-// 3q + 1, 3q + 2; radius cbrt(u0), cos(phi) = 1 - 2 u1, azimuth 2 pi u2.  2D:
-// block m gives samples 2m and 2m + 1; radius sqrt(u0), azimuth 2 pi u1
-// ("Monte-Carlo Integration" section).  ACC selects
+// Philox(1, n, k, stream), ... (four words per block) and sample j takes words 2j
+// and 2j + 1, so block m gives samples 2m and 2m + 1.  3D: three 21-bit uniforms
+// from the two words, radius cbrt(u0), cos(phi) = 1 - 2 u1, azimuth 2 pi u2; 2D:
+// two 24-bit uniforms, radius sqrt(u0), azimuth 2 pi u1 ("Monte-Carlo
+// Integration" section).  ACC selects
 // correctly rounded sqrt / cbrt and the polynomial sine and cosine (used when few
 // samples make per-sample accuracy visible); otherwise the hardware
 // approximations.
-template <int DIM, bool ACC>
-__device__ __forceinline__ void raw_direction2(uint32_t wa, float &d0, float &d1)
+// Raw direction (minus the unit direction) of the azimuth 2 pi m / 2^BITS of an
+// integer m below 2^BITS.
+template <bool ACC, int BITS>
+__device__ __forceinline__ void raw_direction(uint32_t m, float &d0, float &d1)
 {
     if (ACC) {
-        neg_sincos_turn(wa >> 8, d0, d1);
+        neg_sincos_turn(m << (24 - BITS), d0, d1);
     } else {
-        constexpr float ANG = 6.283185307179586f / 16777216.0f;   // 2 pi / 2^24
-        const float ang = fmaf(top24(wa), ANG, -3.14159265358979323846f);
+        constexpr float ANG = 6.283185307179586f / (float)(1u << BITS);   // 2 pi / 2^BITS
+        const float ang = fmaf(__uint2float_rn(m), ANG, -3.14159265358979323846f);
         d0 = cos_approx(ang);
         d1 = sin_approx(ang);
     }
 }
 
+// 3D: the two words of a sample give three 21-bit uniforms -- u0 = w0 bits 31..11,
+// u1 = w1 bits 20..0, u2 = w0 bits 10..0 followed by w1 bits 31..22 -- each times
+// 2^-21.  u0 and u1 are read as the biased floats 2^23 + u (exact, one logic
+// operation each) and scaled and unbiased by one packed FMA (exact).
 template <int DIM, bool ACC, typename Gather>
 __device__ __forceinline__ Terms sample3(const Gather &gat, const IterC<DIM> &ic, const EvolveArgs &a, uint32_t w0,
-                                         uint32_t w1, uint32_t w2)
+                                         uint32_t w1)
 {
-    const float2 ut = mul2(make_float2(top24(w0), top24(w1)), dup2(5.9604644775390625e-8f));
+    const float b0 = __uint_as_float((w0 >> 11) | 0x4B000000u);
+    const float b1 = __uint_as_float((w1 & 0x1FFFFFu) | 0x4B000000u);
+    const uint32_t u2 = __funnelshift_l(w1, w0, 10) & 0x1FFFFFu;
+    const float2 ut = fma2(make_float2(b0, b1), dup2(4.76837158203125e-7f), dup2(-4.0f));   // (b - 2^23) 2^-21
     const float u0 = ut.x, t = ut.y;
     const float rv = ACC ? cbrtf(u0) : ex2_approx(lg2_approx(u0) * (1.0f / 3.0f));
     const float cphi = fmaf(-2.0f, t, 1.0f);
     const float sh = ACC ? sqrtf(t * (1.0f - t)) : sqrt_approx(t * (1.0f - t));
     float c0, s0;
-    raw_direction2<DIM, ACC>(w2, c0, s0);
+    raw_direction<ACC, 21>(u2, c0, s0);
     const float2 d = mul2(dup2(sh), make_float2(c0, s0));
     const float2 x = fma2(mul2(dup2(rv), make_float2(ic.K[0], ic.K[1])), d, make_float2(ic.ax[0].cf, ic.ax[1].cf));
     const float x2 = fmaf(rv * ic.K[2], cphi, ic.ax[2].cf);
@@ -414,7 +423,7 @@ __device__ __forceinline__ Terms sample2(const Gather &gat, const IterC<DIM> &ic
 {
     const float rv = ACC ? sqrtf(top24(wr)) : sqrt_approx(top24(wr));
     float d0, d1;
-    raw_direction2<DIM, ACC>(wa, d0, d1);
+    raw_direction<ACC, 24>(wa >> 8, d0, d1);
     const float2 x = fma2(mul2(dup2(rv), make_float2(ic.K[0], ic.K[1])), make_float2(d0, d1),
                           make_float2(ic.ax[0].cf, ic.ax[1].cf));
     return sample_terms<DIM>(ic, a, rv, gat.at(x.x, x.y, 0.0f), d0, d1, 0.0f);
@@ -425,33 +434,25 @@ __device__ __forceinline__ void sample_contour(const Gather &gat, const IterC<DI
                                                uint32_t n, uint32_t k, uint32_t stream, int lig, Acc &acc)
 {
     if constexpr (DIM == 3) {
-        // a lane takes quads q, q + G, ...: three Philox blocks give its four
-        // samples, summed in two roundings before one compensated addition; the
-        // last N mod 4 samples (the start of quad N / 4) go to one lane
-        const int nq = a.N >> 2;
-        int q = lig;
+        // block m gives samples 2m and 2m + 1; a lane takes blocks m and m + G (four
+        // samples, summed in two roundings before one compensated addition), then a
+        // leftover block, then an odd N's last sample
+        const int pairs = a.N >> 1;
+        int m = lig;
 #pragma unroll 1
-        for (; q < nq; q += G) {
-            const uint4 A = philox4x32_10(make_uint4((uint32_t)(3 * q), n, k, stream), a.rk0, a.rk1);
-            const uint4 B = philox4x32_10(make_uint4((uint32_t)(3 * q + 1), n, k, stream), a.rk0, a.rk1);
-            const uint4 C = philox4x32_10(make_uint4((uint32_t)(3 * q + 2), n, k, stream), a.rk0, a.rk1);
-            add_terms4<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y, A.z),
-                                  sample3<DIM, ACC>(gat, ic, a, A.w, B.x, B.y),
-                                  sample3<DIM, ACC>(gat, ic, a, B.z, B.w, C.x),
-                                  sample3<DIM, ACC>(gat, ic, a, C.y, C.z, C.w));
+        for (; m + G < pairs; m += 2 * G) {
+            const uint4 A = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
+            const uint4 B = philox4x32_10(make_uint4((uint32_t)(m + G), n, k, stream), a.rk0, a.rk1);
+            add_terms4<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y), sample3<DIM, ACC>(gat, ic, a, A.z, A.w),
+                                  sample3<DIM, ACC>(gat, ic, a, B.x, B.y), sample3<DIM, ACC>(gat, ic, a, B.z, B.w));
         }
-        const int rem = a.N & 3;
-        if (rem && lig == nq % G) {
-            const uint4 A = philox4x32_10(make_uint4((uint32_t)(3 * nq), n, k, stream), a.rk0, a.rk1);
-            add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y, A.z));
-            if (rem > 1) {
-                const uint4 B = philox4x32_10(make_uint4((uint32_t)(3 * nq + 1), n, k, stream), a.rk0, a.rk1);
-                add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.w, B.x, B.y));
-                if (rem > 2) {
-                    const uint4 C = philox4x32_10(make_uint4((uint32_t)(3 * nq + 2), n, k, stream), a.rk0, a.rk1);
-                    add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, B.z, B.w, C.x));
-                }
-            }
+        if (m < pairs) {
+            const uint4 A = philox4x32_10(make_uint4((uint32_t)m, n, k, stream), a.rk0, a.rk1);
+            add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y), sample3<DIM, ACC>(gat, ic, a, A.z, A.w));
+        }
+        if ((a.N & 1) && lig == pairs % G) {
+            const uint4 A = philox4x32_10(make_uint4((uint32_t)pairs, n, k, stream), a.rk0, a.rk1);
+            add_terms<DIM, COMP>(acc, sample3<DIM, ACC>(gat, ic, a, A.x, A.y));
         }
     } else {
         // the two samples of a Philox block form a pair; four blocks of a lane (m,

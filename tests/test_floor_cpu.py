@@ -6,7 +6,8 @@ This is the reference the free-running bars of the GPU tests are set against
 trajectories more than 0.25 voxel elsewhere -- contours near saddles between
 touching disks or random-walking on background noise -- and changes up to 0.8 % of
 the localized cells, so no arithmetic, FP64 included, can promise 99.9 % there; on
-the small 3D case (separated balls) nothing moves."""
+the small 3D case (separated balls) at most 0.1 % of the trajectories move (one of
+2,048) and the cells do not change."""
 import math
 
 import numpy as np
@@ -38,4 +39,5 @@ def test_one_ulp_floor_small3d(oracle):
     from paper_1804_06304_gb300 import synth
     s = synth.small_3d(0)
     floor, cells = _floor(oracle, s, 3, 4.0, 256, 50, 1234)
-    assert floor == {"centres_within_0.25": 1.0, "agreement": 1.0, "agreement_0.25": 1.0} and cells >= 18
+    assert floor["centres_within_0.25"] >= 0.999 and cells >= 18, floor
+    assert floor["agreement"] == 1.0 and floor["agreement_0.25"] == 1.0, floor

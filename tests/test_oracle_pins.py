@@ -99,28 +99,48 @@ def test_unit_ball_sampling_is_uniform(oracle, ndim):
         assert np.all(u[:, :2] == u[:, :2])  # finite
 
 
+def test_uniforms21(oracle):
+    """The 3D sample's three 21-bit uniforms: w0 bits 31..11, w1 bits 20..0, and w0
+    bits 10..0 followed by w1 bits 31..22 (w1 bit 21 unused)."""
+    assert oracle.uniforms21(0, 0) == (0.0, 0.0, 0.0)
+    top = 1.0 - 2.0**-21
+    assert oracle.uniforms21(0xFFFFFFFF, 0xFFFFFFFF) == (top, top, top)
+    assert oracle.uniforms21(0x800, 0) == (2.0**-21, 0.0, 0.0)          # lowest bit of u0
+    assert oracle.uniforms21(0x400, 0) == (0.0, 0.0, 0.5)              # highest bit of u2
+    assert oracle.uniforms21(0, 0x400000) == (0.0, 0.0, 2.0**-21)      # lowest bit of u2
+    assert oracle.uniforms21(0, 0x200000) == (0.0, 0.0, 0.0)           # the unused bit
+    assert oracle.uniforms21(0, 0x100000) == (0.0, 0.5, 0.0)           # highest bit of u1
+
+
 @pytest.mark.parametrize("ndim,N", [(3, 67), (2, 33)])
 def test_sample_word_layout(oracle, ndim, N):
-    """Sample j takes words d j .. d j + d - 1 of the stream Philox(0, n, k, s),
-    Philox(1, n, k, s), ...: radius, polar and azimuth angles follow from those words
-    alone (3D: three blocks per four samples; 2D: one block per two)."""
+    """Sample j takes words 2 j and 2 j + 1 of the stream Philox(0, n, k, s),
+    Philox(1, n, k, s), ... (one block per two samples): radius, polar and azimuth
+    angles follow from those two words alone -- 2D: two 24-bit uniforms (one per
+    word); 3D: three 21-bit uniforms cut from the 64 bits (restated here with
+    Python integers)."""
     it, k, sid = 4, 9, 2
     P = oracle.make_params(ndim, N, seed=0x1234567890ABCDEF, stream_id=sid)
-    nb = (ndim * N + 3) // 4
+    nb = (2 * N + 3) // 4
     ctr = np.array([[b, it, k, sid] for b in range(nb)], dtype=np.uint32)
     words = oracle.philox(ctr, [0x90ABCDEF, 0x12345678]).reshape(-1)
     u = oracle.unit_samples(P, it, k)
     for j in range(N):
-        w = [int(x) for x in words[ndim * j: ndim * j + ndim]]
+        w0, w1 = int(words[2 * j]), int(words[2 * j + 1])
+        bits = (w0 << 32) | w1                    # the 64 bits, w0 first
         r = np.linalg.norm(u[j, :ndim])
         if ndim == 3:
-            assert r == pytest.approx(oracle.uniform24(w[0]) ** (1 / 3), rel=1e-12, abs=1e-12)
-            assert u[j, 2] == pytest.approx(r * (1 - 2 * oracle.uniform24(w[1])), abs=1e-12)
+            u0 = (bits >> 43) / 2**21             # bits 63..43 = w0 bits 31..11
+            u1 = (bits & (2**21 - 1)) / 2**21     # bits 20..0 = w1 bits 20..0
+            u2 = ((bits >> 22) & (2**21 - 1)) / 2**21   # bits 42..22 = w0 10..0, w1 31..22
+            assert r == pytest.approx(u0 ** (1 / 3), rel=1e-12, abs=1e-12)
+            assert u[j, 2] == pytest.approx(r * (1 - 2 * u1), abs=1e-12)
         else:
-            assert r == pytest.approx(math.sqrt(oracle.uniform24(w[0])), rel=1e-12, abs=1e-12)
+            u0, u2 = (w0 >> 8) / 2**24, (w1 >> 8) / 2**24
+            assert r == pytest.approx(math.sqrt(u0), rel=1e-12, abs=1e-12)
         if r > 1e-6 and np.hypot(u[j, 0], u[j, 1]) > 1e-9:
             th = math.atan2(u[j, 1], u[j, 0]) % (2 * math.pi)
-            want = 2 * math.pi * oracle.uniform24(w[ndim - 1])
+            want = 2 * math.pi * u2
             assert min(abs(th - want), 2 * math.pi - abs(th - want)) < 1e-9
 
 
