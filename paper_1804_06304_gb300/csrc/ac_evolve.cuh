@@ -249,6 +249,86 @@ template <int DIM, typename T> struct RawFast {
     }
 };
 
+// Raw taps through 32-bit shared-memory addresses (3D fast path; the bounds-checked
+// build keeps RawFast): the directed
+// add leaves bits(t_d) = 2^23 + tap index d (as an integer 0x4B000000 + index), so the
+// byte address of the base tap is C + es bits(t0) + es py bits(t1) + es pz bits(t2)
+// with the biases folded into C (arithmetic modulo 2^32); the other taps are
+// that address plus row / plane pitches, the x+1 taps an immediate offset.
+template <typename T> __device__ __forceinline__ float lds_tap(uint32_t a);
+template <typename T> __device__ __forceinline__ float lds_tap_next(uint32_t a);
+template <> __device__ __forceinline__ float lds_tap<uint16_t>(uint32_t a)
+{
+    unsigned short v;
+    asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return __uint_as_float(0x4B000000u | v);
+}
+template <> __device__ __forceinline__ float lds_tap_next<uint16_t>(uint32_t a)
+{
+    unsigned short v;
+    asm("ld.shared.u16 %0, [%1+2];" : "=h"(v) : "r"(a));
+    return __uint_as_float(0x4B000000u | v);
+}
+template <> __device__ __forceinline__ float lds_tap<uint8_t>(uint32_t a)
+{
+    unsigned short v;
+    asm("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
+    return __uint_as_float(0x4B000000u | v);
+}
+template <> __device__ __forceinline__ float lds_tap_next<uint8_t>(uint32_t a)
+{
+    unsigned short v;
+    asm("ld.shared.u8 %0, [%1+1];" : "=h"(v) : "r"(a));
+    return __uint_as_float(0x4B000000u | v);
+}
+template <> __device__ __forceinline__ float lds_tap<__half>(uint32_t a)
+{
+    unsigned short v;
+    asm("ld.shared.b16 %0, [%1];" : "=h"(v) : "r"(a));
+    return __half2float(__ushort_as_half(v));
+}
+template <> __device__ __forceinline__ float lds_tap_next<__half>(uint32_t a)
+{
+    unsigned short v;
+    asm("ld.shared.b16 %0, [%1+2];" : "=h"(v) : "r"(a));
+    return __half2float(__ushort_as_half(v));
+}
+template <> __device__ __forceinline__ float lds_tap<float>(uint32_t a)
+{
+    float v;
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+template <> __device__ __forceinline__ float lds_tap_next<float>(uint32_t a)
+{
+    float v;
+    asm("ld.shared.f32 %0, [%1+4];" : "=f"(v) : "r"(a));
+    return v;
+}
+
+template <typename T> struct RawFast3S {
+    uint32_t C;      // folded base address (see above)
+    uint32_t pyb, pzb;   // row and plane pitch, bytes
+    float M[3];
+    __device__ __forceinline__ float at(float x0, float x1, float x2) const
+    {
+        constexpr float Z = TapBias<T>::value;
+        constexpr uint32_t es = sizeof(T);
+        const float2 t = __fadd2_rd(make_float2(x0, x1), make_float2(M[0], M[1]));
+        const float2 fr = sub2(make_float2(x0, x1), sub2(t, make_float2(M[0], M[1])));
+        const float t2 = add_rd(x2, M[2]);
+        const float f2 = x2 - (t2 - M[2]);
+        const uint32_t a = C + es * __float_as_uint(t.x) + pyb * __float_as_uint(t.y) + pzb * __float_as_uint(t2);
+        const uint32_t r = a + pzb, ay = a + pyb, ry = r + pyb;
+        const float2 lo0 = make_float2(lds_tap<T>(a), lds_tap<T>(r)), hi0 = make_float2(lds_tap_next<T>(a), lds_tap_next<T>(r));
+        const float2 lo1 = make_float2(lds_tap<T>(ay), lds_tap<T>(ry)), hi1 = make_float2(lds_tap_next<T>(ay), lds_tap_next<T>(ry));
+        const float2 a0 = fma2(dup2(fr.x), sub2(hi0, lo0), Z != 0.0f ? sub2(lo0, dup2(Z)) : lo0);
+        const float2 a1 = fma2(dup2(fr.x), sub2(hi1, lo1), Z != 0.0f ? sub2(lo1, dup2(Z)) : lo1);
+        const float2 sz = fma2(dup2(fr.y), sub2(a1, a0), a0);           // (plane z0, plane z1)
+        return fmaf(f2, sz.y - sz.x, sz.x);
+    }
+};
+
 // Clamped path in shared memory (quads in 2D, raw voxels otherwise).
 template <int DIM, typename T, bool QUAD> struct SmemClamp {
     const void *p;
@@ -706,6 +786,8 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
     }
 
     const int py = a.ext[0], pz = a.ext[0] * a.ext[1];
+    // base of the 32-bit tap addresses of the 3D fast path, biases folded (modulo 2^32)
+    const uint32_t raw_C = smem_u32(smem_raw) - (uint32_t)sizeof(T) * 0x4B000000u * (uint32_t)(1 + py + pz);
     // the staged region's first and last usable tap per axis (within the volume)
     float fr_lo[3], fr_hi[3];
 #pragma unroll
@@ -771,8 +853,19 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
                     QuadFast<QT, QuadOf<T>::diff> gat{Q, qp, {M[0], M[1]}, nquads, V.status};
                     s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
                 } else {
-                    RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}, nraw, V.status};
-                    s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig, mask);
+#ifndef AC_CHECKED
+                    if constexpr (DIM == 3) {   // 32-bit shared addresses, biases folded into raw_C
+                        RawFast3S<T> gat{raw_C, (uint32_t)(sizeof(T) * py), (uint32_t)(sizeof(T) * pz),
+                                         {M[0], M[1], M[2]}};
+                        s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig,
+                                                            mask);
+                    } else
+#endif
+                    {
+                        RawFast<DIM, T> gat{reg, py, pz, {M[0], M[1], M[2]}, nraw, V.status};
+                        s = eval_contour<DIM, G, COMP, ACC>(gat, ic, R, a, n, (uint32_t)k, V.stream, V.scale, lig,
+                                                            mask);
+                    }
                 }
             } else if (inside) {
                 if (quad) {
