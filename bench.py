@@ -57,8 +57,8 @@ ALG_SLOTS_CURRENT = {2: 52.75, 3: 95.25}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
 # ncu capture of the current kernel (to be removed when the kernel changes), scaled
 # with the volume and contour count: the 2048^2 instance of large-2d read 7.02 MB
-# (x 4), the 256x256x64 instance of brain-3d 9.499 MB (x 64).
-DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.1e6, ("brain-3d", "brick", 0, "native"): 607.9e6}
+# (x 4), the 256x256x64 instance of brain-3d 9.497 MB (x 64).
+DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.1e6, ("brain-3d", "brick", 0, "native"): 607.8e6}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0
