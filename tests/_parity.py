@@ -178,7 +178,7 @@ def free_running(ac, oracle, s, vol, ndim, stride, p, r, ids=None):
 
 
 def floor_bar(floor_value):
-    """A free-running bar: the benchmark spec's 0.999, lowered only where the FP64
+    """A free-running bar: 0.999, lowered only where the FP64
     dynamics themselves lose more than 0.033 % after a one-ulp change of the seeds
     (the GPU may lose three times what the worst such change does)."""
     return min(0.999, 1.0 - 3.0 * (1.0 - floor_value))

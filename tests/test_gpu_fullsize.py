@@ -11,8 +11,8 @@ T = 100 iterations, automatic brick plan).  Then:
   lattice from the GPU's own FP32 seeds with the FP32 parameters; final centres
   are compared, and the library's localization of the window's contours is
   compared with the oracle's (detection-set agreement 2 |matched| / (|D_gpu| +
-  |D_oracle|), one-to-one within 0.5 voxel).  The bars are the spec ones
-  (>= 99.9 % of the centres within 0.25 voxel, agreement >= 0.999), lowered only
+  |D_oracle|), one-to-one within 0.5 voxel).  The bars are 99.9 % of the centres
+  within 0.25 voxel and an agreement of at least 0.999, lowered only
   by what the FP64 dynamics themselves show: oracle runs whose seeds differ from
   the first by one FP32 ulp along x, y (and z) measure how many trajectories and
   cells a last-bit change alone moves, and the GPU may lose at most three times
