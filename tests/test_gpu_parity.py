@@ -194,6 +194,31 @@ def test_teacher_forced_storage_types(ac, oracle, brain_small, kind):
     assert frac >= 0.9999, (frac, nflag, worst, bad)
 
 
+@pytest.mark.parametrize("case", ["small3d", "crop2d", "brain_f16"])
+def test_teacher_forced_narrow_magnitudes(ac, oracle, small3d, crop2d, brain_small, case):
+    """The teacher-forced rows judged once more with narrower magnitudes: E against
+    sum |S I| instead of the intensity mass, each dE/dc_a against its own
+    sum |S'(r) u_a I| instead of the direction-free sum.  The tolerance stays 1e-5
+    and the bar 0.9999: the default bar does not rest on the wider magnitudes
+    (every teacher-forced comparison of a session is also judged this way and
+    listed at its end)."""
+    if case == "small3d":
+        s, vol, nd, stride, tk, t0 = small3d, small3d.volume, 3, 4.0, (0, 2048), 0
+        p = _p3(ac, s)
+    elif case == "crop2d":
+        s, vol, nd, stride, tk, t0 = crop2d, crop2d.volume, 2, 6.0, (1000, 2500), 1000
+        p = ac.default_params(2, 6.0 / math.sqrt(1.5), s.contrast, N=128, T=100, seed=99)
+    else:
+        s, vol, nd, stride, tk, t0 = brain_small, brain_small.volume_f16, 3, 6.0, (0, 4096), 0
+        p = ac.default_params(3, 6.0 / math.sqrt(1.5), s.contrast, N=512, T=10, seed=5)
+    r = P.gpu_run(ac, vol, s.spacing, p, stride=stride, trace_k=tk)
+    img = P.oracle_image(oracle, vol, s.spacing)
+    frac, nflag, worst, bad, res = P.teacher_forced(oracle, img, P.oracle_params(oracle, nd, p), r["trace"], t0, 1)
+    narrow, narrow_worst = P.narrow_pass_fraction(oracle, r["trace"], res)
+    assert frac >= 0.9999, (frac, nflag, worst, bad)
+    assert narrow >= 0.9999, (case, narrow, narrow_worst)
+
+
 @pytest.mark.parametrize("N,G", [(115, 4), (112, 4), (100, 4), (31, 8), (9, 16), (130, 16)])
 def test_teacher_forced_2d_ragged(ac, oracle, crop2d, N, G):
     """2D sample counts that exercise every part of a lane's loop: groups of four
