@@ -701,13 +701,10 @@ def batch_arm(args, wl, rank, world, dev):
         for c in C:
             ac.ac_reseed(c)
         ac.ac_plan_launch(plan, use_graph=True)
-        n = 0
-        for i, c in enumerate(C):
-            cells = ac.ac_localize(c, E0)
-            n += len(cells)
-            if keep is not None:
-                keep.append(cells)
-        return n
+        cells = ac.ac_localize_batch(C, E0)   # every set in one pass
+        if keep is not None:
+            keep.extend(cells)
+        return sum(len(c) for c in cells)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):

@@ -320,6 +320,21 @@ typedef struct {
 ac_status ac_localize(ac_contours *ctr, const ac_localize_params *params, ac_cell *out_host,
                       int64_t cap, int64_t *n_out, void *cuda_stream);
 
+/*
+ * ac_localize_batch -- ac_localize of n_sets distinct contour sets in one call
+ * (the batching form: many tiles evolved by one plan).  Set i uses params[i],
+ * writes up to caps[i] cells to out_host[i] (host memory, caller-owned) and its
+ * total count to n_out[i]; the cells of each set are those ac_localize gives for
+ * it alone.  The sets' work is queued phase by phase on one stream, so the call
+ * synchronizes the stream four times (plus once per further eight competition
+ * rounds) whatever n_sets is, instead of several times per set.  Errors:
+ * AC_ERR_ARG (NULL arrays, a NULL or repeated set, a negative cap, a NaN E0), and
+ * the first failing set's AC_ERR_OOM / AC_ERR_CUDA / AC_ERR_TIMEOUT /
+ * AC_ERR_NUMERIC, after which the counts are unspecified.
+ */
+ac_status ac_localize_batch(ac_contours *const *sets, int32_t n_sets, const ac_localize_params *params,
+                            ac_cell *const *out_host, const int64_t *caps, int64_t *n_out, void *cuda_stream);
+
 /* ------------------------------------------------------------------ state ----- */
 /*
  * ac_get_state / ac_set_state -- copy the contour state to / from host memory as

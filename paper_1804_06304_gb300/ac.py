@@ -100,6 +100,9 @@ _SIGS = {
                                    ct.POINTER(ac_evolve_params), ct.c_void_p]),
     "ac_localize": (ct.c_int, [ct.c_void_p, ct.POINTER(ac_localize_params), ct.c_void_p, ct.c_int64,
                                ct.POINTER(ct.c_int64), ct.c_void_p]),
+    "ac_localize_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int32, ct.POINTER(ac_localize_params),
+                                     ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
+                                     ct.c_void_p]),
     "ac_get_state": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "ac_set_state": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "ac_state_device_ptr": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p)]),
@@ -440,6 +443,25 @@ def ac_localize(ctr: Contours, E0: float, cap: int | None = None, stream=None) -
     _check(l.ac_localize(ctr.handle, ct.byref(ac_localize_params(E0)), ct.c_void_p(out.ctypes.data), cap,
                          ct.byref(n), ct.c_void_p(_stream(stream))))
     return out[:min(n.value, cap)]
+
+
+def ac_localize_batch(sets, E0, caps=None, stream=None) -> list:
+    """ac_localize of several distinct contour sets in one call (one threshold for
+    all, or one per set); returns one cell array per set."""
+    l = load()
+    n = len(sets)
+    E0s = [float(E0)] * n if np.isscalar(E0) else [float(e) for e in E0]
+    if len(E0s) != n:
+        raise ValueError("ac_localize_batch: one E0 or one per set")
+    caps = [c.count for c in sets] if caps is None else [int(c) for c in caps]
+    outs = [np.zeros(max(c, 1), dtype=CELL_DTYPE) for c in caps]
+    handles = _handles(sets) if n else (ct.c_void_p * 1)()
+    params = (ac_localize_params * max(n, 1))(*[ac_localize_params(e) for e in E0s])
+    ptrs = (ct.c_void_p * max(n, 1))(*[o.ctypes.data for o in outs])
+    capv = (ct.c_int64 * max(n, 1))(*caps)
+    nout = (ct.c_int64 * max(n, 1))()
+    _check(l.ac_localize_batch(handles, n, params, ptrs, capv, nout, ct.c_void_p(_stream(stream))))
+    return [o[:min(nout[i], caps[i])] for i, o in enumerate(outs)]
 
 
 def ac_get_state(ctr: Contours, stream=None) -> np.ndarray:

@@ -28,6 +28,11 @@ void Scratch::release_all()
     DevBuf *all[] = {&keys, &vals, &skeys, &svals, &cub, &desc, &tmaps, &active, &flags, &surv, &ekeys, &surv_sorted,
                      &pos, &cellk, &celli, &cellk_s, &celli_s, &cell_start, &stat, &acc, &cells, &counters};
     for (DevBuf *b : all) b->release();
+    lsets.release();
+    und.release();
+    hcount.release();
+    hcells.release();
+    hsets.release();
 }
 
 }  // namespace ac
@@ -387,19 +392,24 @@ void ac::destroy_contours_on(ac_contours *ctr, cudaStream_t st)
 extern "C" void ac_destroy_contours(ac_contours *ctr) { ac::destroy_contours_on(ctr, nullptr); }
 
 // ------------------------------------------------------------------ state
+ac_status ac::status_error(int32_t w)
+{
+    if (w & STATUS_TMA_TIMEOUT) AC_FAIL(AC_ERR_TIMEOUT, "device status: a brick load did not complete in time");
+    if (w & STATUS_LOCALIZE_LIMIT) AC_FAIL(AC_ERR_TIMEOUT, "device status: localization round bound reached");
+    if (w & STATUS_NONFINITE) AC_FAIL(AC_ERR_NUMERIC, "device status: non-finite contour state");
+    if (w & STATUS_BOUNDS)
+        AC_FAIL(AC_ERR_STATE, "device status: a gather index left its array (bounds-checked build)");
+    if (w & STATUS_GRID_RANGE)
+        AC_FAIL(AC_ERR_ARG, "device status: a contour radius exceeded the grid path's bound (contour stopped)");
+    return AC_OK;
+}
+
 static ac_status check_status(ac_contours *ctr, cudaStream_t st)
 {
     int32_t s[4];
     AC_CUDA(cudaMemcpyAsync(s, ctr->status, sizeof(s), cudaMemcpyDeviceToHost, st));
     AC_CUDA(cudaStreamSynchronize(st));
-    if (s[0] & STATUS_TMA_TIMEOUT) AC_FAIL(AC_ERR_TIMEOUT, "device status: a brick load did not complete in time");
-    if (s[0] & STATUS_LOCALIZE_LIMIT) AC_FAIL(AC_ERR_TIMEOUT, "device status: localization round bound reached");
-    if (s[0] & STATUS_NONFINITE) AC_FAIL(AC_ERR_NUMERIC, "device status: non-finite contour state");
-    if (s[0] & STATUS_BOUNDS)
-        AC_FAIL(AC_ERR_STATE, "device status: a gather index left its array (bounds-checked build)");
-    if (s[0] & STATUS_GRID_RANGE)
-        AC_FAIL(AC_ERR_ARG, "device status: a contour radius exceeded the grid path's bound (contour stopped)");
-    return AC_OK;
+    return status_error(s[0]);
 }
 
 extern "C" ac_status ac_get_state(ac_contours *ctr, float *out_host, void *cuda_stream)
@@ -1743,8 +1753,28 @@ extern "C" ac_status ac_localize(ac_contours *ctr, const ac_localize_params *par
     g_err.clear();
     if (!ctr || !params || !n_out || cap < 0 || (cap > 0 && !out_host)) AC_FAIL(AC_ERR_ARG, "ac_localize: bad arguments");
     if (std::isnan(params->E0)) AC_FAIL(AC_ERR_ARG, "ac_localize: E0 is NaN");
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    ac_status s = check_status(ctr, st);
-    if (s != AC_OK) return s;
-    return localize_impl(ctr, params->E0, out_host, cap, n_out, st);
+    *n_out = 0;
+    return localize_many(&ctr, &params->E0, &out_host, &cap, n_out, 1, (cudaStream_t)cuda_stream);
+}
+
+extern "C" ac_status ac_localize_batch(ac_contours *const *sets, int32_t n_sets, const ac_localize_params *params,
+                                       ac_cell *const *out_host, const int64_t *caps, int64_t *n_out,
+                                       void *cuda_stream)
+{
+    ac::Range nvtx_range("ac_localize_batch");
+    g_err.clear();
+    if (n_sets < 0 || (n_sets > 0 && (!sets || !params || !out_host || !caps || !n_out)))
+        AC_FAIL(AC_ERR_ARG, "ac_localize_batch: bad arguments");
+    std::vector<float> E0((size_t)n_sets);
+    for (int32_t i = 0; i < n_sets; ++i) {
+        if (!sets[i] || caps[i] < 0 || (caps[i] > 0 && !out_host[i]))
+            AC_FAIL(AC_ERR_ARG, "ac_localize_batch: bad arguments for set " + std::to_string(i));
+        if (std::isnan(params[i].E0)) AC_FAIL(AC_ERR_ARG, "ac_localize_batch: E0 is NaN for set " + std::to_string(i));
+        for (int32_t j = 0; j < i; ++j)
+            if (sets[j] == sets[i]) AC_FAIL(AC_ERR_ARG, "ac_localize_batch: a contour set appears twice");
+        E0[(size_t)i] = params[i].E0;
+        n_out[i] = 0;
+    }
+    if (n_sets == 0) return AC_OK;
+    return localize_many(sets, E0.data(), out_host, caps, n_out, n_sets, (cudaStream_t)cuda_stream);
 }

@@ -51,10 +51,37 @@ struct DevBuf {
     template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+// Grow-only page-locked host buffer (device-to-host copies that do not block the
+// host until the stream reaches them).
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes + bytes / 4 + 256;
+        cudaError_t e = cudaMallocHost(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
 struct Scratch {
     DevBuf keys, vals, skeys, svals, cub, desc, tmaps, active;       // evolve
     DevBuf flags, surv, ekeys, surv_sorted, pos, cellk, celli, cellk_s, celli_s, cell_start, stat, acc,
         cells, counters;                                               // localize
+    DevBuf lsets, und;                                                 // localize: set descriptors, open counts
+    HostBuf hcount, hcells, hsets;                                     // localize: read back / uploaded
     void release_all();
 };
 
@@ -132,9 +159,16 @@ void destroy_volume_on(ac_volume *vol, cudaStream_t st);
 // (nullptr: no trace); drops the plan's captured graph.  Used by the request loop.
 ac_status plan_set_trace(ac_plan *plan, int set, const ac_trace *trace);
 
-// localization (ac_localize.cu); returns an ac_status and sets the message
-ac_status localize_impl(ac_contours *ctr, float E0, ac_cell *out_host, int64_t cap, int64_t *n_out,
-                        cudaStream_t st);
+// localization (ac_localize.cu) of n distinct sets in one pass on one stream,
+// each with its own threshold, host output and cap; the first set's scratch holds
+// the batch's buffers.  The whole batch synchronizes the stream four times (plus
+// once per further eight competition rounds).  Returns an ac_status (the first
+// failing set's) and sets the message.
+ac_status localize_many(ac_contours *const *sets, const float *E0, ac_cell *const *out_host, const int64_t *cap,
+                        int64_t *n_out, int n, cudaStream_t st);
+
+// the error a device status word reports (AC_OK if none), message set (ac_api.cu)
+ac_status status_error(int32_t word);
 
 }  // namespace ac
 

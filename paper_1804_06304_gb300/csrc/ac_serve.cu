@@ -127,23 +127,41 @@ std::string last_error(const char *what)
     return std::string(what) + (m.empty() ? "" : ": " + m);
 }
 
-// Localizes tiles whose last round ended at event `after`, on the localization
-// stream (so the round launched since keeps the GPU busy), keeps their cells and
-// releases their memory in stream order behind the localization.
+// Localizes tiles whose last round ended at event `after`, all in one pass on the
+// localization stream (so the round launched since keeps the GPU busy), keeps
+// their cells and releases their memory in stream order behind the localization.
 void retire(ac_server *S, std::vector<Tile *> &tiles, cudaEvent_t after)
 {
     if (tiles.empty()) return;
     cudaStreamWaitEvent(S->loc_st, after, 0);
-    std::vector<std::pair<ac_status, std::string>> outcome;
-    for (Tile *t : tiles) {
-        t->cells.resize((size_t)std::max<int64_t>(1, t->contours));
-        int64_t n_out = 0;
-        ac_localize_params lp{S->p.E0};
-        std::swap(t->ctr->scratch, S->loc_scratch);
-        ac_status ls = ac_localize(t->ctr, &lp, t->cells.data(), (int64_t)t->cells.size(), &n_out, S->loc_st);
-        std::swap(t->ctr->scratch, S->loc_scratch);
-        outcome.emplace_back(ls, ls == AC_OK ? std::string() : last_error("localize"));
-        t->n_cells = ls == AC_OK ? n_out : 0;
+    const size_t nt = tiles.size();
+    std::vector<std::pair<ac_status, std::string>> outcome(nt, {AC_OK, std::string()});
+    std::vector<ac_contours *> sets(nt);
+    std::vector<ac_cell *> outs(nt);
+    std::vector<float> E0(nt, S->p.E0);
+    std::vector<int64_t> caps(nt), n_out(nt, 0);
+    for (size_t i = 0; i < nt; ++i) {
+        tiles[i]->cells.resize((size_t)std::max<int64_t>(1, tiles[i]->contours));
+        sets[i] = tiles[i]->ctr;
+        outs[i] = tiles[i]->cells.data();
+        caps[i] = (int64_t)tiles[i]->cells.size();
+    }
+    // every finished tile in one pass, the server's buffers lent to the first; if
+    // that fails, each tile alone, so that a failure is reported for its own tile
+    std::swap(sets[0]->scratch, S->loc_scratch);
+    ac_status ls =
+        ac::localize_many(sets.data(), E0.data(), outs.data(), caps.data(), n_out.data(), (int)nt, S->loc_st);
+    std::swap(sets[0]->scratch, S->loc_scratch);
+    if (ls != AC_OK)
+        for (size_t i = 0; i < nt; ++i) {
+            std::swap(sets[i]->scratch, S->loc_scratch);
+            const ac_status li = ac::localize_many(&sets[i], &E0[i], &outs[i], &caps[i], &n_out[i], 1, S->loc_st);
+            std::swap(sets[i]->scratch, S->loc_scratch);
+            outcome[i] = {li, li == AC_OK ? std::string() : last_error("localize")};
+        }
+    for (size_t i = 0; i < nt; ++i) {
+        Tile *t = tiles[i];
+        t->n_cells = outcome[i].first == AC_OK ? n_out[i] : 0;
         t->cells.resize((size_t)std::min<int64_t>(t->n_cells, (int64_t)t->cells.size()));
         t->cells.shrink_to_fit();
         release_device(t, S->loc_st);

@@ -105,3 +105,51 @@ def test_autotune_leaves_sets_and_passes_parity(ac, oracle, vols):
     img = P.oracle_image(oracle, s.volume, s.spacing)
     frac, nflag, worst, bad, _ = P.teacher_forced(oracle, img, P.oracle_params(oracle, 3, tuned), r["trace"], 0, 1)
     assert frac >= 0.9999, (frac, worst, bad)
+
+
+def test_localize_batch_equals_each_set_and_the_oracle(ac, oracle, vols):
+    """One ac_localize_batch over uneven 3D sets, a 2D set, a set that the energy
+    cull empties, an explicitly empty set and a cap below the accepted count gives
+    every set exactly the cells of ac_localize alone, which are the oracle's."""
+    from paper_1804_06304_gb300 import synth
+    keep = []
+    sets = _sets(ac, vols, keep)
+    ac.ac_evolve_batch(sets, _params(ac, T=20))
+    s2 = synth.large_2d(4, shape=(256, 256), n_nuclei=60)
+    V2 = ac.ac_create_volume(s2.volume, s2.spacing)
+    C2 = ac.ac_seed(V2, stride=6.0)
+    ac.ac_evolve(C2, ac.default_params(2, 6.0 / math.sqrt(1.5), s2.contrast, N=128, T=20, seed=3))
+    V0 = ac.ac_create_volume(np.zeros((8, 8, 8), np.uint8))
+    C0 = ac.ac_seed(V0, explicit=np.zeros((0, 4), np.float32))
+    Ecut = ac.ac_seed(ac.ac_create_volume(vols[0].volume), stride=4.0)   # E = 0 at seeding: culled by E0 < 0
+    all_sets = sets + [C2, C0, Ecut]
+    E0 = [ac.default_E0(3, 170.0)] * len(sets) + [ac.default_E0(2, s2.contrast), -1.0, -1.0]
+    alone = [ac.ac_localize(c, e) for c, e in zip(all_sets, E0)]
+    assert len(alone[0]) > 3 and len(alone[-2]) == 0 and len(alone[-1]) == 0
+    got = ac.ac_localize_batch(all_sets, E0)
+    for a, b in zip(alone, got):
+        np.testing.assert_array_equal(a, b)
+    for c, e, cells in zip(all_sets[:len(sets) + 1], E0, got):
+        st = ac.ac_get_state(c).astype(np.float64)
+        nd = 2 if c is C2 else 3
+        assert list(cells["id"]) == list(oracle.localize(nd, st[:4].T, st[4], float(np.float32(e))))
+    caps = [2] + [c.count for c in all_sets[1:]]
+    part = ac.ac_localize_batch(all_sets, E0, caps=caps)
+    np.testing.assert_array_equal(part[0], alone[0][:2])
+    for a, b in zip(alone[1:], part[1:]):
+        np.testing.assert_array_equal(a, b)
+    assert ac.ac_localize_batch([], 0.0) == []
+
+
+def test_localize_batch_rejects_bad_arguments(ac, vols):
+    keep = []
+    sets = _sets(ac, vols[:2], keep)
+    with pytest.raises(ac.ACError) as e:
+        ac.ac_localize_batch([sets[0], sets[1], sets[0]], 0.0)
+    assert e.value.status == ac.AC_ERR_ARG
+    with pytest.raises(ac.ACError) as e:
+        ac.ac_localize_batch(sets, [0.0, float("nan")])
+    assert e.value.status == ac.AC_ERR_ARG
+    with pytest.raises(ac.ACError) as e:
+        ac.ac_localize_batch(sets, 0.0, caps=[5, -1])
+    assert e.value.status == ac.AC_ERR_ARG

@@ -65,10 +65,15 @@ def test_localize_round_bound(ac, oracle, small3d):
     ac.ac_evolve(C, p)
     st = ac.ac_get_state(C)
     E0 = 1e9                                       # every contour survives the energy cull
+    C2 = ac.ac_seed(V, stride=4.0)
+    ac.ac_evolve(C2, p)
     try:
         ac.ac_set_wait_limits(localize_rounds=0)
         with pytest.raises(ac.ACError) as e:
             ac.ac_localize(C, E0)
+        assert e.value.status == ac.AC_ERR_TIMEOUT and "round bound" in str(e.value)
+        with pytest.raises(ac.ACError) as e:          # the same bound in a batch
+            ac.ac_localize_batch([C2], E0)
         assert e.value.status == ac.AC_ERR_TIMEOUT and "round bound" in str(e.value)
     finally:
         ac.ac_set_wait_limits(-1, -1)
@@ -81,6 +86,12 @@ def test_localize_round_bound(ac, oracle, small3d):
     cells = ac.ac_localize(C, E0)
     want = oracle.localize(3, st[:4].T.astype(np.float64), st[4].astype(np.float64), E0)
     assert list(cells["id"]) == list(want)
+    with pytest.raises(ac.ACError) as e:            # the batch's set keeps its failure too
+        ac.ac_get_state(C2)
+    assert e.value.status == ac.AC_ERR_TIMEOUT
+    ac.ac_reseed(C2)
+    ac.ac_evolve(C2, p)
+    assert list(ac.ac_localize_batch([C2], E0)[0]["id"]) == list(want)
 
 
 def test_server_wait_times_out_on_an_unfinished_tile(ac):
