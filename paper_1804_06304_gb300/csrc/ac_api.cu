@@ -81,10 +81,61 @@ static float clamp_box(float c, const ac_volume *v, int d)
     return c < 0.0f ? 0.0f : (c > hi ? hi : c);
 }
 
+namespace {
+// The row-pitched copy of a device array with element strides (1, rs, ps):
+// block row blockIdx.y is plane z0 + blockIdx.y, threads run over its elements.
+template <typename E>
+__global__ void repack_kernel(const E *src, int64_t rs, int64_t ps, E *dst, int64_t pitch_y, int64_t nx, int64_t ny,
+                              int64_t z0)
+{
+    const int64_t z = z0 + blockIdx.y;
+    const int64_t plane = nx * ny;
+    const E *s = src + z * ps;
+    E *d = dst + z * ny * pitch_y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = plane < ((int64_t)1 << 32) ? (int64_t)((uint32_t)i / (uint32_t)nx) : i / nx;
+        const int64_t x = i - y * nx;
+        d[y * pitch_y + x] = s[y * rs + x];
+    }
+}
+
+template <typename E>
+cudaError_t repack_t(const ac_volume *v, const void *src, int64_t rs, int64_t ps, cudaStream_t st)
+{
+    const int64_t plane = v->n[0] * v->n[1];
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((plane + 255) / 256, 2048));
+    for (int64_t z0 = 0; z0 < v->n[2]; z0 += 65535) {
+        const unsigned gy = (unsigned)std::min<int64_t>(65535, v->n[2] - z0);
+        repack_kernel<E><<<dim3(gx, gy), 256, 0, st>>>(static_cast<const E *>(src), rs, ps, static_cast<E *>(v->data),
+                                                       v->pitch_y, v->n[0], v->n[1], z0);
+        count_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t repack(const ac_volume *v, const void *src, int64_t rs, int64_t ps, cudaStream_t st)
+{
+    switch (v->es) {
+    case 1: return repack_t<uint8_t>(v, src, rs, ps, st);
+    case 2: return repack_t<uint16_t>(v, src, rs, ps, st);
+    default: return repack_t<uint32_t>(v, src, rs, ps, st);
+    }
+}
+}  // namespace
+
 // Copy voxels with element strides (1, row_stride, plane_stride) into the
-// row-pitched device copy of `v`.
-static cudaError_t copy_voxels(const ac_volume *v, const void *data, int data_on_device, int64_t row_stride,
-                               int64_t plane_stride, cudaStream_t st)
+// row-pitched device copy of `v`.  Device voxels are repacked by a kernel.  Dense
+// host voxels whose rows need padding go up in one contiguous copy and are
+// repacked on the device (a 2D copy of short rows runs at a few GB/s): through a
+// stream-ordered temporary when a volume is created, through a staging buffer
+// that the volume keeps when voxels are loaded again (`keep_staging`); volumes of
+// a request loop (allocated from its pool) copy row by row instead, so that they
+// hold no memory beyond what the loop's budget charges.  Strided host voxels are
+// copied row by row.
+static cudaError_t copy_voxels(ac_volume *v, const void *data, int data_on_device, int64_t row_stride,
+                               int64_t plane_stride, cudaStream_t st, bool keep_staging)
 {
     const int64_t *n = v->n;
     const int es = v->es;
@@ -92,8 +143,30 @@ static cudaError_t copy_voxels(const ac_volume *v, const void *data, int data_on
     const size_t pitch = (size_t)v->pitch_y * es;
     const cudaMemcpyKind kind = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const char *src = (const char *)data;
-    if (pitch == row_bytes && row_stride == n[0] && plane_stride == row_stride * n[1])
-        return cudaMemcpyAsync(v->data, src, v->bytes, kind, st);
+    const bool dense = row_stride == n[0] && plane_stride == row_stride * n[1];
+    if (pitch == row_bytes && dense) return cudaMemcpyAsync(v->data, src, v->bytes, kind, st);
+    if (data_on_device) return repack(v, data, row_stride, plane_stride, st);
+    if (dense && !v->pool) {
+        const size_t dense_bytes = row_bytes * (size_t)n[1] * (size_t)n[2];
+        cudaError_t e;
+        if (keep_staging) {
+            if (v->staging_bytes < dense_bytes) {
+                if (v->staging) cudaFree(v->staging);
+                v->staging = nullptr;
+                v->staging_bytes = 0;
+                if ((e = cudaMalloc(&v->staging, dense_bytes)) != cudaSuccess) return e;
+                v->staging_bytes = dense_bytes;
+            }
+            if ((e = cudaMemcpyAsync(v->staging, src, dense_bytes, kind, st)) != cudaSuccess) return e;
+            return repack(v, v->staging, n[0], n[0] * n[1], st);
+        }
+        void *tmp = nullptr;
+        if ((e = cudaMallocAsync(&tmp, dense_bytes, st)) != cudaSuccess) return e;
+        e = cudaMemcpyAsync(tmp, src, dense_bytes, kind, st);
+        if (e == cudaSuccess) e = repack(v, tmp, n[0], n[0] * n[1], st);
+        const cudaError_t f = cudaFreeAsync(tmp, st);
+        return e != cudaSuccess ? e : f;
+    }
     if (plane_stride == row_stride * n[1])
         return cudaMemcpy2DAsync(v->data, pitch, src, (size_t)row_stride * es, row_bytes, (size_t)(n[1] * n[2]), kind, st);
     cudaError_t e = cudaSuccess;
@@ -161,7 +234,7 @@ static ac_status create_volume_impl(cudaMemPool_t pool, const void *data, int da
         AC_FAIL(e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA,
                 std::string("ac_create_volume: allocation: ") + cudaGetErrorString(e));
     }
-    e = copy_voxels(v, data, data_on_device, row_stride, plane_stride, st);
+    e = copy_voxels(v, data, data_on_device, row_stride, plane_stride, st, false);
     if (e != cudaSuccess) {
         dev_free(v->data, pool, st);
         delete v;
@@ -200,7 +273,7 @@ extern "C" ac_status ac_load_volume(ac_volume *vol, const void *data, int data_o
     if (plane_stride == 0) plane_stride = row_stride * vol->n[1];
     if (row_stride < vol->n[0] || plane_stride < row_stride * vol->n[1])
         AC_FAIL(AC_ERR_ARG, "ac_load_volume: strides smaller than the extents");
-    AC_CUDA(copy_voxels(vol, data, data_on_device, row_stride, plane_stride, (cudaStream_t)cuda_stream));
+    AC_CUDA(copy_voxels(vol, data, data_on_device, row_stride, plane_stride, (cudaStream_t)cuda_stream, true));
     return AC_OK;
 }
 
@@ -208,6 +281,7 @@ void ac::destroy_volume_on(ac_volume *vol, cudaStream_t st)
 {
     if (!vol) return;
     dev_free(vol->data, vol->pool, st);
+    if (vol->staging) cudaFree(vol->staging);
     delete vol;
 }
 

@@ -23,6 +23,8 @@ struct ac_volume {
     int64_t pitch_z;      // elements per plane
     size_t bytes;
     cudaMemPool_t pool;   // non-null: `data` is a stream-ordered allocation from this pool
+    void *staging = nullptr;     // dense voxels uploaded by ac_load_volume, repacked on the device
+    size_t staging_bytes = 0;
 };
 
 namespace ac {

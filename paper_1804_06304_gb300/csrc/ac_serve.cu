@@ -378,9 +378,14 @@ extern "C" ac_status ac_server_create(const ac_server_params *params, ac_server 
     S->p.evolve.first_iter = 0;
     S->p.evolve.update_last = 0;
     cudaError_t e = cudaGetDevice(&S->device);
+    // The upload and localization streams run at the highest priority: a round's
+    // evolution fills every SM, and their short kernels (seeding, localization)
+    // then take SMs as the round's blocks retire instead of waiting for its end.
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->up_st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->loc_st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->up_st, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->loc_st, cudaStreamNonBlocking, prio_high);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&S->ev_round[i], cudaEventDisableTiming);
     if (e == cudaSuccess) {
         // the tiles' memory pool keeps up to the budget cached between tiles
