@@ -303,8 +303,9 @@ ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, int ndim, con
  * overlaps it, overlap meaning |c' - c''| < rho_d max(R', R''), rho_3 = 2^(-1/3),
  * rho_2 = 2^(-1/2).  Writes up to `cap` cells (host memory) in acceptance order and
  * the total count to *n_out (which may exceed cap).  Cell radius = rho_d R.
- * Synchronizes the stream.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA,
- * AC_ERR_TIMEOUT / AC_ERR_NUMERIC when the status word is set.
+ * Synchronizes the stream.  Errors: AC_ERR_ARG (also for 2^31 or more contours),
+ * AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_TIMEOUT / AC_ERR_NUMERIC when the status word is
+ * set.
  */
 typedef struct {
     float E0;           /* energy threshold */
@@ -327,10 +328,12 @@ ac_status ac_localize(ac_contours *ctr, const ac_localize_params *params, ac_cel
  * total count to n_out[i]; the cells of each set are those ac_localize gives for
  * it alone.  The sets' work is queued phase by phase on one stream, so the call
  * synchronizes the stream four times (plus once per further eight competition
- * rounds) whatever n_sets is, instead of several times per set.  Errors:
- * AC_ERR_ARG (NULL arrays, a NULL or repeated set, a negative cap, a NaN E0), and
- * the first failing set's AC_ERR_OOM / AC_ERR_CUDA / AC_ERR_TIMEOUT /
- * AC_ERR_NUMERIC, after which the counts are unspecified.
+ * rounds) whatever n_sets is, instead of several times per set.  The first set's
+ * handle holds the call's temporary buffers (sized for the whole batch).  Errors:
+ * AC_ERR_ARG (NULL arrays, a NULL or repeated set, a negative cap, a NaN E0, more
+ * than 65535 sets or 2^31 - 1 contours in one call), and the first failing set's
+ * AC_ERR_OOM / AC_ERR_CUDA / AC_ERR_TIMEOUT / AC_ERR_NUMERIC, after which the
+ * counts are unspecified.
  */
 ac_status ac_localize_batch(ac_contours *const *sets, int32_t n_sets, const ac_localize_params *params,
                             ac_cell *const *out_host, const int64_t *caps, int64_t *n_out, void *cuda_stream);
