@@ -636,13 +636,15 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     pl.acc = p->sampling == 1 || (p->sampling == 0 && p->N < 64);
     if (pl.acc && !pl.comp) AC_FAIL(AC_ERR_ARG, "ac_evolve: accurate sampling is built with compensated sums only");
     // lanes per contour: 2D about 32 samples per lane (4 lanes only with compensated
-    // sums and fast sampling, otherwise at least 8); 3D about 8 to 16 (a warp per
-    // contour at N = 512); at most 32
+    // sums and fast sampling, otherwise at least 8); 3D about 8 to 16, except that
+    // 512 <= N < 1024 takes 16 lanes (32 samples per lane, two contours per warp:
+    // measured best at N = 512); at most 32
     int G = p->lanes_per_contour;
     if (G == 0) {
-        if (vol->ndim == 3) {   // 3D: a warp per contour unless N is small (measured best at N = 512)
+        if (vol->ndim == 3) {
             G = 8;
             while (G < 32 && (int64_t)G * 8 < p->N) G *= 2;
+            if (p->N >= 512 && p->N < 1024) G = 16;
         } else {
             G = (pl.comp && !pl.acc) ? 4 : 8;
             while (G < 32 && (int64_t)G * 32 < p->N) G *= 2;
@@ -656,9 +658,12 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     // 3D regions are kept within half the shared memory so two CTAs share an SM
     const int64_t budget = vol->ndim == 3 ? 110 * 1024 : 200 * 1024;
     int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
-    // lattice cells per brick: 2x2x2 in 3D, 10x8 in 2D (measured best for 128
-    // samples: 80 contours of 4 lanes fill 10 warps, two CTAs per SM at 96 registers)
-    int cells[3] = {vol->ndim == 3 ? 2 : 10, vol->ndim == 3 ? 2 : 8, 2};
+    // lattice cells per brick: 2x2x2 in 3D (2x4x2 with 16 lanes per contour, so 16
+    // contours fill 8 warps; the longer axis is y, because a row of 64 16-bit voxels
+    // would put every row of the region on the same shared-memory banks), 10x8 in 2D
+    // (measured best for 128 samples: 80 contours of 4 lanes fill 10 warps, two CTAs
+    // per SM at 96 registers)
+    int cells[3] = {vol->ndim == 3 ? 2 : 10, vol->ndim == 3 ? (G == 16 ? 4 : 2) : 8, 2};
     auto brick_of = [&](int d) {
         const int b = p->brick[d] ? p->brick[d] : (int)std::lround(cells[d] * stride_hint / vol->sp[d]);
         return std::max(1, std::min(b, (int)std::min<int64_t>(vol->n[d], 224)));
@@ -697,6 +702,10 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
                 const int64_t cap = vol->n[d] + (d == 0 ? al - 1 : 0);
                 need = std::min(need, cap);
                 if (d == 0) need = (need + al - 1) / al * al;
+                // 3D taps are read from the raw region: a row of a multiple of 128 bytes
+                // would put the same voxel column of every row on one shared-memory bank,
+                // so such rows get 16 more bytes (unless the region spans the volume's rows)
+                if (d == 0 && vol->ndim == 3 && need < vol->n[0] && need * vol->es % 128 == 0) need += al;
                 if (need > 256) fits_box = false;
                 ext = (int)need;
             }
@@ -1645,7 +1654,7 @@ extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_ev
     }
     std::vector<std::array<int, 3>> cells;
     if (v0->ndim == 2) cells = {{8, 8, 1}, {10, 8, 1}, {12, 8, 1}, {16, 8, 1}};
-    else cells = {{2, 2, 2}, {2, 2, 1}, {3, 3, 2}, {4, 4, 2}};
+    else cells = {{2, 2, 2}, {2, 4, 2}, {2, 2, 1}, {3, 3, 2}, {4, 4, 2}};
 
     // trial copies of the contour states (trials must not move the real contours)
     std::vector<ac_contours> tmp(n_sets);

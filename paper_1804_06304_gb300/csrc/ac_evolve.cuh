@@ -680,6 +680,19 @@ template <int G> __device__ __forceinline__ unsigned group_mask()
     return ((1u << (G & 31)) - 1u) << (lane & ~(unsigned)(G - 1));
 }
 
+// Votes over the whole warp.  With one contour per warp (G = 32) its lanes agree
+// already, so the vote is the lane's own value.
+template <int G> __device__ __forceinline__ bool warp_any(bool p)
+{
+    if constexpr (G == 32) return p;
+    else return __any_sync(0xffffffffu, p);
+}
+template <int G> __device__ __forceinline__ bool warp_all(bool p)
+{
+    if constexpr (G == 32) return p;
+    else return __all_sync(0xffffffffu, p);
+}
+
 // Evaluate one contour-iteration with the chosen gather, reduce over the group.
 template <int DIM, int G, bool COMP, bool ACC, typename Gather>
 __device__ __forceinline__ Step eval_contour(const Gather &gat, const IterC<DIM> &ic, float R, const EvolveArgs &a,
@@ -800,54 +813,83 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
     const int lig = threadIdx.x % G;
     const int grp = threadIdx.x / G;
     const int ngrp = blockDim.x / G;
+    const int wsub = grp % (32 / G);   // this group's place among the groups of its warp
     const unsigned mask = group_mask<G>();
     const int64_t C = V.C;
     unsigned int n_fast = 0, n_clamped = 0, n_global = 0;   // this group's contour-iterations per gather path
 
-    for (int64_t i = cb + grp; i < ce; i += ngrp) {
-        const int64_t k = (int64_t)a.sorted_gidx[i] - V.contour_base;
-        int32_t h = V.hold ? V.hold[k] : 0;
-        if (h & HOLD_STOPPED) continue;   // stopped by a rule in an earlier call
-        float c[3] = {V.state[k], V.state[C + k], DIM == 3 ? V.state[2 * C + k] : 0.0f};
-        float R = V.state[3 * C + k];
-        Step s;
+    // The groups of a warp walk the brick's contours together (slots wi + wsub), so
+    // that every lane of the warp reaches the per-iteration path votes below; a group
+    // without a contour, or whose contour has stopped, idles through them.
+    for (int64_t wi = cb + (grp - wsub); wi < ce; wi += ngrp) {
+        const int64_t i = wi + wsub;
+        bool live = i < ce;
+        int64_t k = 0;
+        int32_t h = 0;
+        if (live) {
+            k = (int64_t)a.sorted_gidx[i] - V.contour_base;
+            h = V.hold ? V.hold[k] : 0;
+            live = !(h & HOLD_STOPPED);   // stopped by a rule in an earlier call
+        }
+        const bool owned = live;          // this group writes the contour back
+        float c[3] = {0.0f, 0.0f, 0.0f}, R = 0.0f;
+        if (live) {
+            c[0] = V.state[k];
+            c[1] = V.state[C + k];
+            if (DIM == 3) c[2] = V.state[2 * C + k];
+            R = V.state[3 * C + k];
+        }
+        Step s = {0.0f, 0.0f, {0.0f, 0.0f, 0.0f}};
         for (int n = V.first_iter; n <= V.last_iter; ++n) {
+            if (!warp_any<G>(live)) break;
             IterC<DIM> ic;
-            iter_consts<DIM>(ic, c, R, V, a);
-            // where do the taps of the whole ball fall (clamped like the samples)?
-            const float Ro = R + 0.5f * a.dR;
-            // fast path: every tap index ci + floor(cf - e) .. ci + floor(cf + e) + 1
-            // inside the volume and the staged region, i.e. per axis
-            // cf - e >= r0 - ci and cf + e < min(n - 1, r0 + ext - 1) - ci (lo = -ci)
-            // (3D; in 2D the full test below is as cheap)
-            bool fast = DIM == 3;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                const AxisSplit &x = ic.ax[d];
-                const float e = fmaf(Ro, V.inv_sp[d], 1e-3f);
-                fast = fast && (x.cf - e >= fr_lo[d] + x.lo) && (x.cf + e < fr_hi[d] + x.lo);
-            }
-            bool inside = fast, interior = fast;
-            if (!fast) {
-                inside = true;
-                interior = true;
+            bool inside = true, interior = true;
+            int o[3] = {0, 0, 0};
+            if (live) {
+                iter_consts<DIM>(ic, c, R, V, a);
+                // where do the taps of the whole ball fall (clamped like the samples)?
+                const float Ro = R + 0.5f * a.dR;
+                // fast path: every tap index ci + floor(cf - e) .. ci + floor(cf + e) + 1
+                // inside the volume and the staged region, i.e. per axis
+                // cf - e >= r0 - ci and cf + e < min(n - 1, r0 + ext - 1) - ci (lo = -ci)
+                // (3D; in 2D the full test below is as cheap)
+                bool fast = DIM == 3;
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
                     const AxisSplit &x = ic.ax[d];
                     const float e = fmaf(Ro, V.inv_sp[d], 1e-3f);
-                    interior = interior && (x.cf - e >= x.lo) && (x.cf + e < x.hi);
-                    const float lo = fminf(fmaxf(x.cf - e, x.lo), x.hi);
-                    const float hi = fminf(fmaxf(x.cf + e, x.lo), x.hi);
-                    const int tlo = x.ci + (int)fminf(floorf(lo), x.top);
-                    const int thi = x.ci + (int)fminf(floorf(hi), x.top) + 1;
-                    inside = inside && tlo >= r0[d] && thi < r0[d] + a.ext[d];
+                    fast = fast && (x.cf - e >= fr_lo[d] + x.lo) && (x.cf + e < fr_hi[d] + x.lo);
                 }
+                inside = fast;
+                interior = fast;
+                if (!fast) {
+                    inside = true;
+                    interior = true;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        const AxisSplit &x = ic.ax[d];
+                        const float e = fmaf(Ro, V.inv_sp[d], 1e-3f);
+                        interior = interior && (x.cf - e >= x.lo) && (x.cf + e < x.hi);
+                        const float lo = fminf(fmaxf(x.cf - e, x.lo), x.hi);
+                        const float hi = fminf(fmaxf(x.cf + e, x.lo), x.hi);
+                        const int tlo = x.ci + (int)fminf(floorf(lo), x.top);
+                        const int thi = x.ci + (int)fminf(floorf(hi), x.top) + 1;
+                        inside = inside && tlo >= r0[d] && thi < r0[d] + a.ext[d];
+                    }
+                }
+                o[0] = ic.ax[0].ci - r0[0];
+                o[1] = ic.ax[1].ci - r0[1];
+                o[2] = DIM == 3 ? ic.ax[2].ci - r0[2] : 0;
             }
-            const int o[3] = {ic.ax[0].ci - r0[0], ic.ax[1].ci - r0[1], DIM == 3 ? ic.ax[2].ci - r0[2] : 0};
-            n_fast += (inside && interior) ? 1u : 0u;
-            n_clamped += (inside && !interior) ? 1u : 0u;
-            n_global += inside ? 0u : 1u;
-            if (inside && interior) {
+            // Several contours per warp take the slowest path any of them needs (every
+            // path gives the same bits), so their lanes never run two paths in turn.
+            const bool use_fast = warp_all<G>(inside && interior);
+            const bool use_smem = warp_all<G>(inside);
+            if (!live) continue;
+            n_fast += use_fast ? 1u : 0u;
+            n_clamped += (use_smem && !use_fast) ? 1u : 0u;
+            n_global += use_smem ? 0u : 1u;
+            if (use_fast) {
                 const float M[3] = {8388608.0f + (float)o[0], 8388608.0f + (float)o[1], 8388608.0f + (float)o[2]};
                 if (quad) {
                     QuadFast<QT, QuadOf<T>::diff> gat{Q, qp, {M[0], M[1]}, nquads, V.status};
@@ -867,7 +909,7 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
                                                             mask);
                     }
                 }
-            } else if (inside) {
+            } else if (use_smem) {
                 if (quad) {
                     SmemClamp<DIM, T, true> gat{Q, qp, 0, {ic.ax[0], ic.ax[1], ic.ax[2]}, {o[0], o[1], o[2]},
                                                 nquads, V.status};
@@ -885,11 +927,12 @@ __global__ void __maxnreg__(DIM == 2 ? 96 : 128) evolve_brick_kernel(const __gri
             if (lig == 0) write_trace(a, v, k, n, c, R, s);
             if (!finite_step(s)) {
                 if (lig == 0) atomicOr(V.status, STATUS_NONFINITE);
-                break;
+                live = false;
+            } else if (step_or_stop<DIM>(s, n, a, V, c, R, h)) {
+                live = false;
             }
-            if (step_or_stop<DIM>(s, n, a, V, c, R, h)) break;
         }
-        if (lig == 0) {
+        if (owned && lig == 0) {
             V.state[k] = c[0];
             V.state[C + k] = c[1];
             if (DIM == 3) V.state[2 * C + k] = c[2];
