@@ -56,9 +56,9 @@ ALG_SLOTS_PER_SAMPLE = {2: 52.75, 3: 102.25}
 ALG_SLOTS_CURRENT = {2: 52.75, 3: 95.25}
 # dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
 # ncu capture of the current kernel (to be removed when the kernel changes), scaled
-# with the volume and contour count: the 2048^2 instance of large-2d read 7.02 MB
-# (x 4), the 256x256x64 instance of brain-3d 9.497 MB (x 64).
-DRAM_BYTES_PER_LAUNCH = {("large-2d", "brick", 0, "native"): 28.1e6, ("brain-3d", "brick", 0, "native"): 607.8e6}
+# with the volume and contour count: the 256x256x64 instance of brain-3d read
+# 9.501 MB (x 64).
+DRAM_BYTES_PER_LAUNCH = {("brain-3d", "brick", 0, "native"): 608.0e6}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0
@@ -565,7 +565,7 @@ def main(argv=None):
             "frac_current_formulation": ALG_SLOTS_CURRENT[ndim] * samples / (k_ms * 1e-3) / 1e12 / peak,
             "traffic": traffic,
             "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: ncu capture of a "
-                            "smaller instance (2048^2 / 256x256x64) scaled with the volume", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
+                            "smaller instance (256x256x64) scaled with the volume", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
             "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
             "alg_slots_per_sample_current": ALG_SLOTS_CURRENT[ndim],
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
