@@ -637,14 +637,14 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     if (pl.acc && !pl.comp) AC_FAIL(AC_ERR_ARG, "ac_evolve: accurate sampling is built with compensated sums only");
     // lanes per contour: 2D about 32 samples per lane (4 lanes only with compensated
     // sums and fast sampling, otherwise at least 8); 3D about 8 to 16, except that
-    // 512 <= N < 1024 takes 16 lanes (32 samples per lane, two contours per warp:
+    // 512 <= N < 1024 takes 8 lanes (64 samples per lane, four contours per warp:
     // measured best at N = 512); at most 32
     int G = p->lanes_per_contour;
     if (G == 0) {
         if (vol->ndim == 3) {
             G = 8;
             while (G < 32 && (int64_t)G * 8 < p->N) G *= 2;
-            if (p->N >= 512 && p->N < 1024) G = 16;
+            if (p->N >= 512 && p->N < 1024) G = 8;
         } else {
             G = (pl.comp && !pl.acc) ? 4 : 8;
             while (G < 32 && (int64_t)G * 32 < p->N) G *= 2;
@@ -655,15 +655,26 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     pl.quad_off = 0;
     if (!pl.brick) return AC_OK;
     const int al = 16 / vol->es;
-    // 3D regions are kept within half the shared memory so two CTAs share an SM
-    const int64_t budget = vol->ndim == 3 ? 110 * 1024 : 200 * 1024;
     int B[3] = {1, 1, 1}, h[3] = {0, 0, 0};
-    // lattice cells per brick: 2x2x2 in 3D (2x4x2 with 16 lanes per contour, so 16
-    // contours fill 8 warps; the longer axis is y, because a row of 64 16-bit voxels
-    // would put every row of the region on the same shared-memory banks), 10x8 in 2D
-    // (measured best for 128 samples: 80 contours of 4 lanes fill 10 warps, two CTAs
-    // per SM at 96 registers)
-    int cells[3] = {vol->ndim == 3 ? 2 : 10, vol->ndim == 3 ? (G == 16 ? 4 : 2) : 8, 2};
+    // lattice cells per brick.  3D: 2x2x2 (8 contours of 32 lanes fill 8 warps, two
+    // CTAs per SM), 2x4x2 with 16 lanes (the longer axis is y, because a row of 64
+    // 16-bit voxels would put every row of the region on the same shared-memory
+    // banks), and with 8 lanes at N >= 512, 4x4x4 (64 contours fill 16 warps, one CTA
+    // per SM with a region of up to 215 KB).  2D: 10x8 (measured best for 128
+    // samples: 80 contours of 4 lanes fill 10 warps, two CTAs per SM at 96 registers).
+    int cells[3] = {10, 8, 2};
+    if (vol->ndim == 3) {
+        cells[0] = cells[1] = cells[2] = 2;
+        if (G == 16) cells[1] = 4;
+        if (G == 8 && p->N >= 512) cells[0] = cells[1] = cells[2] = 4;
+    }
+    // groups for the contours of a brick (lattice estimate), 1..16 warps
+    auto warps_of = [&]() {
+        if (p->warps_per_block) return p->warps_per_block;
+        double per = 1.0;
+        for (int d = 0; d < vol->ndim; ++d) per *= std::max(1.0, B[d] * (double)vol->sp[d] / stride_hint);
+        return std::max(1, std::min(16, (int)std::ceil(per * G / 32.0)));
+    };
     auto brick_of = [&](int d) {
         const int b = p->brick[d] ? p->brick[d] : (int)std::lround(cells[d] * stride_hint / vol->sp[d]);
         return std::max(1, std::min(b, (int)std::min<int64_t>(vol->n[d], 224)));
@@ -692,6 +703,10 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
             B[dm] = brick_of(dm);
         }
     }
+    // The staged region may take the shared memory its CTA's registers leave it: in 3D
+    // (128 registers a thread) a CTA of more than 8 warps has its SM alone, smaller ones
+    // share it with a second CTA.
+    const int64_t budget = vol->ndim == 3 ? (warps_of() > 8 ? 215 * 1024 : 110 * 1024) : 200 * 1024;
     for (int iter = 0; iter < 4096; ++iter) {
         int64_t raw = vol->es;
         bool fits_box = true;
@@ -724,13 +739,7 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
             pl.raw = (int)raw;
             pl.quad_off = (int)quad_off;
             pl.smem = (int)total;
-            if (p->warps_per_block == 0) {
-                // enough groups for the contours of a brick (lattice estimate), 1..16 warps
-                double per = 1.0;
-                for (int d = 0; d < vol->ndim; ++d) per *= std::max(1.0, B[d] * (double)vol->sp[d] / stride_hint);
-                const int w = (int)std::ceil(per * G / 32.0);
-                pl.warps = std::max(1, std::min(16, w));
-            }
+            pl.warps = warps_of();
             return AC_OK;
         }
         int hmax = 0, bmax = 0;
@@ -1654,7 +1663,7 @@ extern "C" ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_ev
     }
     std::vector<std::array<int, 3>> cells;
     if (v0->ndim == 2) cells = {{8, 8, 1}, {10, 8, 1}, {12, 8, 1}, {16, 8, 1}};
-    else cells = {{2, 2, 2}, {2, 4, 2}, {2, 2, 1}, {3, 3, 2}, {4, 4, 2}};
+    else cells = {{2, 2, 2}, {2, 4, 2}, {2, 2, 1}, {3, 3, 2}, {4, 4, 2}, {4, 4, 4}};
 
     // trial copies of the contour states (trials must not move the real contours)
     std::vector<ac_contours> tmp(n_sets);
