@@ -258,6 +258,30 @@ void ac_destroy_plan(ac_plan *plan);
 ac_status ac_autotune(ac_contours *const *sets, int32_t n_sets, ac_evolve_params *params, void *cuda_stream);
 
 /*
+ * ac_plan_layout -- the launch layout ac_evolve takes for one contour set of a
+ * volume with these extents, voxel type and spacing, seeded with lattice stride
+ * `stride` and largest initial radius `r0` (as ac_seed records them), under
+ * *params.  The layout is how the brick path of the "Parallel Contour
+ * Evaluation" section is laid out on this GPU: lanes per contour, warps per CTA,
+ * the brick interior and its halo, and the region each CTA stages into shared
+ * memory.  Host logic only (no device work, no allocation): it may be called
+ * without a GPU.  dims: x, y, z (z ignored in 2D); spacing likewise.  The
+ * plain and grid paths report their lanes and warps; their brick, halo,
+ * region and smem_bytes are 0.  Errors: AC_ERR_ARG for the arguments
+ * ac_evolve rejects, or a region that cannot fit shared memory.
+ */
+typedef struct {
+    int32_t lanes_per_contour;   /* lanes of a warp that share one contour's samples   */
+    int32_t warps_per_block;     /* warps per CTA                                       */
+    int32_t brick[3];            /* brick interior, voxels per axis (x, y, z)           */
+    int32_t halo[3];             /* halo beyond the brick, voxels per axis              */
+    int32_t region[3];           /* staged region per CTA (the TMA box), voxels         */
+    int32_t smem_bytes;          /* dynamic shared memory per CTA                       */
+} ac_layout;
+ac_status ac_plan_layout(int32_t ndim, ac_dtype dtype, const int64_t dims[3], const float spacing[3], double stride,
+                         double r0, const ac_evolve_params *params, ac_layout *out);
+
+/*
  * ac_evolve_static -- ac_evolve for callers that cannot allocate device memory.
  * Some callers must not call cudaMalloc: code whose device memory is owned by
  * its own allocator (a framework's caching allocator that has reserved the free

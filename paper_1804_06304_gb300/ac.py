@@ -55,6 +55,11 @@ class ac_batch_item(ct.Structure):
                 ("update_last", ct.c_int32)]
 
 
+class ac_layout(ct.Structure):
+    _fields_ = [("lanes_per_contour", ct.c_int32), ("warps_per_block", ct.c_int32), ("brick", ct.c_int32 * 3),
+                ("halo", ct.c_int32 * 3), ("region", ct.c_int32 * 3), ("smem_bytes", ct.c_int32)]
+
+
 class ac_localize_params(ct.Structure):
     _fields_ = [("E0", ct.c_float)]
 
@@ -114,6 +119,8 @@ _SIGS = {
     "ac_evolve_static": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(ct.c_int64), ct.c_int64, ct.c_int64,
                                     ct.POINTER(ct.c_float), ct.c_float, ct.c_void_p, ct.c_int64, ct.c_float,
                                     ct.c_float, ct.POINTER(ac_evolve_params), ct.c_void_p]),
+    "ac_plan_layout": (ct.c_int, [ct.c_int32, ct.c_int, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_float), ct.c_double,
+                                  ct.c_double, ct.POINTER(ac_evolve_params), ct.POINTER(ac_layout)]),
     "ac_plan_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ac_batch_item), ct.c_int32,
                                   ct.POINTER(ac_evolve_params), ct.POINTER(ct.c_void_p)]),
     "ac_plan_rebind": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(ac_batch_item), ct.c_int32,
@@ -515,6 +522,20 @@ def ac_evolve_stops(ctr: Contours, stream=None) -> tuple:
 
 def ac_kernel_launches() -> int:
     return int(load().ac_kernel_launches())
+
+
+def ac_plan_layout(ndim: int, dtype: int, dims, spacing, stride: float, r0: float, params: EvolveParams) -> dict:
+    """The launch layout ac_evolve takes for one contour set (host logic; no GPU
+    needed): dims and spacing are (x, y[, z]); returns lanes_per_contour,
+    warps_per_block, brick, halo, region (voxels, x y z) and smem_bytes."""
+    d = (ct.c_int64 * 3)(*(list(dims) + [1] * 3)[:3])
+    sp = (ct.c_float * 3)(*[float(v) for v in (list(spacing) + [1.0] * 3)[:3]])
+    out = ac_layout()
+    p = params.to_c()
+    _check(load().ac_plan_layout(int(ndim), int(dtype), d, sp, float(stride), float(r0), ct.byref(p), ct.byref(out)))
+    return {"lanes_per_contour": out.lanes_per_contour, "warps_per_block": out.warps_per_block,
+            "brick": tuple(out.brick), "halo": tuple(out.halo), "region": tuple(out.region),
+            "smem_bytes": out.smem_bytes}
 
 
 AC_STATIC_MAX_CONTOURS = 1 << 20

@@ -706,8 +706,8 @@ ac_status plan_evolve(const ac_volume *vol, double stride_hint, double r_hint, c
     // The staged region may take the shared memory its CTA's registers leave it: in 3D
     // (128 registers a thread) a CTA of more than 8 warps has its SM alone, smaller ones
     // share it with a second CTA.
-    const int64_t budget = vol->ndim == 3 ? (warps_of() > 8 ? 215 * 1024 : 110 * 1024) : 200 * 1024;
     for (int iter = 0; iter < 4096; ++iter) {
+        const int64_t budget = vol->ndim == 3 ? (warps_of() > 8 ? 215 * 1024 : 110 * 1024) : 200 * 1024;
         int64_t raw = vol->es;
         bool fits_box = true;
         for (int d = 0; d < 3; ++d) {
@@ -1239,6 +1239,52 @@ ac_status static_scratch_ptr(int dev, unsigned char **out)
 }
 
 }  // namespace
+
+extern "C" ac_status ac_plan_layout(int32_t ndim, ac_dtype dtype, const int64_t dims[3], const float spacing[3],
+                                    double stride, double r0, const ac_evolve_params *p, ac_layout *out)
+{
+    g_err.clear();
+    if (!dims || !spacing || !p || !out) AC_FAIL(AC_ERR_ARG, "ac_plan_layout: NULL argument");
+    ac_status s = check_params(p);
+    if (s != AC_OK) return s;
+    const int es = elem_size(dtype);
+    if (es == 0) AC_FAIL(AC_ERR_ARG, "ac_plan_layout: unknown dtype");
+    if (ndim != 2 && ndim != 3) AC_FAIL(AC_ERR_ARG, "ac_plan_layout: ndim must be 2 or 3");
+    if (!(stride > 0.0) || !(r0 > 0.0) || !std::isfinite(stride) || !std::isfinite(r0))
+        AC_FAIL(AC_ERR_ARG, "ac_plan_layout: stride and r0 must be positive");
+    ac_volume vol;   // geometry only: nothing on the device
+    vol.device = -1;
+    vol.dtype = dtype;
+    vol.ndim = ndim;
+    vol.es = es;
+    vol.scale = 1.0f;
+    vol.data = nullptr;
+    vol.bytes = 0;
+    vol.pool = nullptr;
+    for (int d = 0; d < 3; ++d) {
+        vol.n[d] = d < ndim ? dims[d] : 1;
+        vol.sp[d] = d < ndim ? spacing[d] : 1.0f;
+        if (d < ndim && (vol.n[d] < 2 || vol.n[d] > (1 << 30) || !(vol.sp[d] > 0.0f) || !std::isfinite(vol.sp[d])))
+            AC_FAIL(AC_ERR_ARG, "ac_plan_layout: every used dimension must be in [2, 2^30] with positive spacing");
+    }
+    vol.pitch_y = vol.n[0];
+    vol.pitch_z = vol.n[0] * vol.n[1];
+    Plan pl;
+    s = plan_evolve(&vol, stride, r0, p, pl);
+    if (s != AC_OK) return s;
+    std::memset(out, 0, sizeof(*out));
+    out->lanes_per_contour = pl.G;
+    out->warps_per_block = pl.warps;
+    if (pl.brick) {
+        for (int d = 0; d < 3; ++d) {
+            out->brick[d] = d < ndim ? pl.B[d] : 1;
+            out->halo[d] = d < ndim ? pl.halo[d] : 0;
+            out->region[d] = pl.ext[d];
+        }
+        out->smem_bytes = pl.smem;
+    }
+    return AC_OK;
+}
 
 extern "C" ac_status ac_evolve_static(const void *volume_dev, ac_dtype dtype, int ndim, const int64_t dims[3],
                                       int64_t row_stride, int64_t plane_stride, const float spacing[3],

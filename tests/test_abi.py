@@ -77,6 +77,7 @@ def test_struct_layouts_match_header(ac, tmp_path):
         "ac_seed_params": ["stride", "R0"],
         "ac_localize_params": ["E0"],
         "ac_batch_item": ["stream_id", "first_iter", "n_iter", "update_last"],
+        "ac_layout": ["lanes_per_contour", "warps_per_block", "brick", "halo", "region", "smem_bytes"],
         "ac_server_params": ["evolve", "dtype", "ndim", "stride", "R0", "E0", "iters_per_round", "max_resident",
                              "hbm_budget_bytes", "max_resident_contours", "balance_rounds"],
         "ac_tile_result": ["ticket", "status", "rounds", "n_cells", "contours", "voxels", "est_bytes", "queue_ms",
