@@ -15,7 +15,10 @@ input already in HBM; `e2e` repeats the step through the same C ABI from pinned
 host memory (host-to-device copy of the image and device-to-host copy of the cells
 inside the timed region).  The roofline entry covers the evolution kernel (plain
 ALU issue bound), `cpu_baseline` times the FP64 oracle on the host cores on a
-bounded sample of the same workload.
+bounded sample of the same workload.  On one GPU the default line also records,
+under `forms`, short runs of the batching form (64 uneven volumes in one
+autotuned, graph-replayed plan) and the serving form (the request loop's
+throughput and tile latencies), each in a child process after the timed steps.
 
 With torchrun (N > 1) every rank processes its own image (weak scaling, replicas:
 contours never interact across images); the step time is the maximum over ranks.
@@ -399,6 +402,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 reference measurement")
     ap.add_argument("--count", type=int, default=0, help="batch-3d: number of volumes (profiling captures)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="brain-3d: skip the short batching and serving runs recorded under `forms`")
     args = ap.parse_args(argv)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -658,9 +663,47 @@ def main(argv=None):
             "roofline": roof, "other_roofs": other, "vs_plain_fp32": plain,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         }
+        if args.workload == "brain-3d" and world == 1 and not args.no_forms and not args.size:
+            line["forms"] = run_forms()
         print(json.dumps(line))
     if dist_on:
         dist.destroy_process_group()
+
+
+def run_forms(timeout_s: float = 900.0) -> dict:
+    """The batching and serving forms, each run briefly in a child process of this
+    script after the timed steps (batch-3d: 3 warm-up and 3 timed steps; serve-3d:
+    its 32 requests saturated, under Poisson arrivals and under a binding HBM
+    budget; no CPU baseline), summarized for the default bench line."""
+    out = {}
+    for name, extra in (("batch-3d", ["--steps", "3", "--warmup", "3"]), ("serve-3d", [])):
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--no-cpu-baseline", *extra]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+            d = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+        except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+            r, d = None, None
+            out[name] = {"error": type(e).__name__}
+            continue
+        if d is None:
+            out[name] = {"error": f"exit {r.returncode}: " + r.stderr.strip()[-300:]}
+            continue
+        f = {"command": " ".join(["python bench.py", "--workload", name, "--no-cpu-baseline", *extra]),
+             "value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"], "steps": d["steps"],
+             "e2e": {k: d["e2e"].get(k) for k in ("value", "ms_per_step")},
+             "roofline_frac": d["roofline"]["frac"], "gpu_launches": d.get("gpu_launches"), "clocks": d.get("clocks"),
+             "autotuned": d["config"].get("autotuned")}
+        if name == "batch-3d":
+            f["evolve_kernel_ms"] = d["roofline"].get("kernel_ms")
+            f["detection_f"] = (d.get("detection") or {}).get("f")
+        else:
+            sv = d["serving"]
+            f["latency_ms"] = {"saturated_p50": sv["saturated_latency_ms_p50"], "poisson_p50": sv["latency_ms_p50"],
+                               "poisson_p99": sv["latency_ms_p99"], "poisson_lambda_hz": sv["poisson_lambda_hz"]}
+            f["saturated_tiles_per_s"] = sv["saturated_tiles_per_s"]
+            f["budget_bound"] = sv.get("budget_bound_saturated")
+        out[name] = f
+    return out
 
 
 def batch_arm(args, wl, rank, world, dev):
