@@ -57,11 +57,14 @@ import numpy as np  # noqa: E402
 # block per two samples) have a leaner count of their own, 95.25, reported beside.
 ALG_SLOTS_PER_SAMPLE = {2: 52.75, 3: 102.25}
 ALG_SLOTS_CURRENT = {2: 52.75, 3: 95.25}
-# dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from an
-# ncu capture of the current kernel (to be removed when the kernel changes), scaled
-# with the volume and contour count: the 256x256x64 instance of brain-3d read
-# 9.498 MB (x 64).
-DRAM_BYTES_PER_LAUNCH = {("brain-3d", "brick", 0, "native"): 607.9e6}
+# dram__bytes_read.sum + dram__bytes_write.sum of the evolve kernel per launch, from
+# ncu captures of the current kernel (to be removed when the kernel changes): brain-3d
+# at full size (one pass: 759.12 MB read + 54.86 MB written); large-2d from its
+# 2048^2 instance (7.42 MB read + 0.04 MB written) scaled with the image (x 4).
+DRAM_BYTES_PER_LAUNCH = {
+    ("brain-3d", "brick", 0, "native"): (814.0e6, "ncu capture of the full-size launch"),
+    ("large-2d", "brick", 0, "native"): (29.9e6, "ncu capture of the 2048^2 instance scaled with the image (x 4)"),
+}
 SM_COUNT = 152
 LANES_PER_SM_CLOCK = 128          # 4 schedulers x 32 lanes, one instruction per clock
 SM_MAX_MHZ = 2070.0
@@ -565,12 +568,12 @@ def main(argv=None):
 
     achieved = ALG_SLOTS_PER_SAMPLE[ndim] * samples / (k_ms * 1e-3) / 1e12
     peak = SM_COUNT * LANES_PER_SM_CLOCK * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = DRAM_BYTES_PER_LAUNCH.get((args.workload, args.path, args.size, args.dtype))
+    traffic, traffic_src = DRAM_BYTES_PER_LAUNCH.get((args.workload, args.path, args.size, args.dtype), (None, None))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s", "frac": achieved / peak,
             "frac_current_formulation": ALG_SLOTS_CURRENT[ndim] * samples / (k_ms * 1e-3) / 1e12 / peak,
             "traffic": traffic,
-            "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: ncu capture of a "
-                            "smaller instance (256x256x64) scaled with the volume", "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
+            "traffic_note": None if traffic is None else "DRAM bytes per evolve launch: " + traffic_src,
+            "kernel": "evolve_brick_kernel" if args.path == "brick" else "evolve_plain_kernel",
             "kernel_ms": k_ms, "alg_slots_per_sample": ALG_SLOTS_PER_SAMPLE[ndim],
             "alg_slots_per_sample_current": ALG_SLOTS_CURRENT[ndim],
             "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM_CLOCK} lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)"}
