@@ -37,6 +37,20 @@ def run_cases() -> dict:
     ac.ac_evolve(C, dataclasses.replace(base3, Rmin=0.5, Rmax=9.0))
     out["b3_global"] = ac.ac_get_state(C)
     out["b3_global_paths"] = np.array(ac.ac_evolve_stats(C))
+    # the full-size brick layouts of a brain-like volume: 8 lanes on 4x4x4-cell bricks in
+    # one 16-warp CTA per SM (a 209.7 KB region whose 128-byte rows are padded to 144),
+    # and 16 lanes on 4x2x2-cell bricks (padded rows, two CTAs per SM); four and two
+    # contours per warp share a gather path
+    sb = synth.brain_3d(4, shape=(256, 256, 64), n_nuclei=1563, with_f16=False)
+    Rb = 6.0 / math.sqrt(1.5)
+    baseb = ac.default_params(3, Rb, sb.contrast, N=512, T=4, seed=13)
+    for name, kw in [("brain_g8", dict(lanes_per_contour=8, brick=(24, 24, 12), warps_per_block=16)),
+                     ("brain_g16", dict(lanes_per_contour=16, brick=(24, 12, 6)))]:
+        V = ac.ac_create_volume(sb.volume, sb.spacing)
+        C = ac.ac_seed(V, stride=6.0)
+        ac.ac_evolve(C, dataclasses.replace(baseb, **kw))
+        out[name] = ac.ac_get_state(C)
+        out[name + "_paths"] = np.array(ac.ac_evolve_stats(C))
     # 2D: half-precision quads (u8), float quads (u16, f32)
     s2 = synth.large_2d(1, shape=(256, 256), n_nuclei=47)
     R2 = 6.0 / math.sqrt(1.5)
