@@ -684,29 +684,36 @@ def run_forms(timeout_s: float = 900.0) -> dict:
         try:
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
             d = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
-        except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+        except (subprocess.TimeoutExpired, OSError, ValueError, IndexError) as e:
             r, d = None, None
             out[name] = {"error": type(e).__name__}
             continue
         if d is None:
             out[name] = {"error": f"exit {r.returncode}: " + r.stderr.strip()[-300:]}
             continue
-        f = {"command": " ".join(["python bench.py", "--workload", name, "--no-cpu-baseline", *extra]),
-             "value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"], "steps": d["steps"],
-             "e2e": {k: d["e2e"].get(k) for k in ("value", "ms_per_step")},
-             "roofline_frac": d["roofline"]["frac"], "gpu_launches": d.get("gpu_launches"), "clocks": d.get("clocks"),
-             "autotuned": d["config"].get("autotuned")}
-        if name == "batch-3d":
-            f["evolve_kernel_ms"] = d["roofline"].get("kernel_ms")
-            f["detection_f"] = (d.get("detection") or {}).get("f")
-        else:
-            sv = d["serving"]
-            f["latency_ms"] = {"saturated_p50": sv["saturated_latency_ms_p50"], "poisson_p50": sv["latency_ms_p50"],
-                               "poisson_p99": sv["latency_ms_p99"], "poisson_lambda_hz": sv["poisson_lambda_hz"]}
-            f["saturated_tiles_per_s"] = sv["saturated_tiles_per_s"]
-            f["budget_bound"] = sv.get("budget_bound_saturated")
-        out[name] = f
+        try:
+            out[name] = _form_summary(name, extra, d)
+        except (KeyError, TypeError) as e:   # a side run never takes the headline line down with it
+            out[name] = {"error": f"unexpected output ({type(e).__name__}: {e})"}
     return out
+
+
+def _form_summary(name: str, extra: list, d: dict) -> dict:
+    f = {"command": " ".join(["python bench.py", "--workload", name, "--no-cpu-baseline", *extra]),
+         "value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"], "steps": d["steps"],
+         "e2e": {k: (d.get("e2e") or {}).get(k) for k in ("value", "ms_per_step")},
+         "roofline_frac": d["roofline"]["frac"], "gpu_launches": d.get("gpu_launches"), "clocks": d.get("clocks"),
+         "autotuned": d["config"].get("autotuned")}
+    if name == "batch-3d":
+        f["evolve_kernel_ms"] = d["roofline"].get("kernel_ms")
+        f["detection_f"] = (d.get("detection") or {}).get("f")
+    else:
+        sv = d["serving"]
+        f["latency_ms"] = {"saturated_p50": sv["saturated_latency_ms_p50"], "poisson_p50": sv["latency_ms_p50"],
+                           "poisson_p99": sv["latency_ms_p99"], "poisson_lambda_hz": sv["poisson_lambda_hz"]}
+        f["saturated_tiles_per_s"] = sv["saturated_tiles_per_s"]
+        f["budget_bound"] = sv.get("budget_bound_saturated")
+    return f
 
 
 def batch_arm(args, wl, rank, world, dev):
