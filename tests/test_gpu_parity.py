@@ -306,6 +306,25 @@ def test_brick_and_plain_paths_agree_bitwise(ac, small3d):
     np.testing.assert_array_equal(a["final"], b["final"])
 
 
+def test_warp_path_vote_leaves_results_unchanged(ac, small3d):
+    """With several contours per warp the warp takes the slowest gather path any of its
+    contours needs.  Every path gives the same bits, so the final states cannot depend
+    on which contours share a warp: 8 lanes per contour (four contours per warp) on
+    three brick layouts -- the planner's, 4x4x4-cell bricks in one 16-warp CTA, 2x4x2
+    cells in 4 warps -- and on the plain path (global gathers only) agree bit for bit."""
+    s = small3d
+    base = _p3(ac, s, T=20, lanes_per_contour=8)
+    runs = []
+    for kw in (dict(), dict(brick=(16, 16, 16), warps_per_block=16), dict(brick=(8, 16, 8)), dict(path=1)):
+        r = P.gpu_run(ac, s.volume, s.spacing, dataclasses.replace(base, **kw), stride=4.0)
+        if kw.get("path") != 1:
+            fast, clamped, glob = ac.ac_evolve_stats(r["ctr"])
+            assert fast + clamped + glob == 2048 * 20 and clamped > 0, (kw, fast, clamped, glob)
+        runs.append(r["final"])
+    for kw, x in zip(("16-warp", "4-warp", "plain"), runs[1:]):
+        np.testing.assert_array_equal(x, runs[0], err_msg=kw)
+
+
 def test_resume_equals_uninterrupted(ac, small3d):
     s = small3d
     full = P.gpu_run(ac, s.volume, s.spacing, _p3(ac, s, T=30), stride=4.0)
